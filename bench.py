@@ -1,0 +1,370 @@
+"""Benchmark: harmonic summing + detection of the SKA-sized plane on GB300.
+
+One step = one hs_run over the whole plane (85 templates x 2^21 bins, FP32,
+H = 16 levels, 1e-8 false-alarm thresholds): every level sum of every point
+is formed, tested and the candidates compacted.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--dtype f32|bf16] [--workload ska|small]
+
+value      : points harmonic-summed per second (85 * 2^21 points per plane per
+             step, all 16 levels), plane resident in HBM, whole job (all ranks).
+e2e        : the same metric through hs_run_host with the plane in pinned host
+             memory: host->device copy, summing, candidate read-back per step.
+roofline   : the staged kernel's algorithmic bytes per launch (plane once +
+             thresholds + candidate records) / its mean event-timed duration,
+             against the measured HBM copy bandwidth.
+cpu_baseline: the FP64 oracle on a bounded sample of the same plane, all host
+             cores (threads over bin ranges).
+--impl reference: the oracle alone, timed on the host cores (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FOP points harmonic-summed/s (H=16) and effective HBM GB/s vs 8 TB/s"
+UNIT = "points/s"
+L2_BYTES = 129 * 2**20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ska", choices=["ska", "small"])
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"])
+    ap.add_argument("--order", type=int, default=0)
+    ap.add_argument("--tile-bins", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target CPU work of the oracle sample (core-seconds)")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_1805_12258_gb300 import synth
+    return synth.ska_plane(seed=1) if name == "ska" else synth.small_plane(seed=0)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---- clocks ------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---- CPU oracle leg --------------------------------------------------------------
+
+def oracle_sample(plane, ta, H, cpu_seconds, threads):
+    """Time the FP64 oracle on all rows x a bin window; returns a dict."""
+    import oracle
+    oracle.build()
+    nt, n = plane.shape
+    mid = n // 2
+    # calibrate: per-point cost on a small window, one thread
+    cal = 2048
+    t0 = time.perf_counter()
+    oracle.detect(plane, H, ta, f_lo=mid, f_hi=mid + cal, threads=1)
+    per_point = (time.perf_counter() - t0) / (nt * cal)
+    bins = int(cpu_seconds / max(per_point, 1e-12) / nt)
+    bins = max(threads * 64, min(bins, n - mid))
+    t0 = time.perf_counter()
+    cands, _ = oracle.detect(plane, H, ta, f_lo=mid, f_hi=mid + bins, threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": nt * bins / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"all {nt} rows x bins [{mid}, {mid + bins}) of the same plane "
+                      f"({nt * bins} points, {H} levels, FP64), {threads} threads",
+            "seconds": dt, "candidates_in_sample": int(len(cands))}
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("hs_staged.cu", "hs_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1805_12258_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(name):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    e = d.get(name)
+    if not e or e.get("kernel_sha") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+# ---- reference arm: the oracle on the host cores ----------------------------------
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1805_12258_gb300 import synth
+    wl = workload(args.workload)
+    plane = synth.make_plane(wl)
+    ta = synth.thresholds(wl.p_fa, wl.H, wl.n_templates)
+    cores = host_cores()
+    per_step = max(2.0, min(args.cpu_seconds, 8.0))
+    for _ in range(args.warmup):
+        oracle_sample(plane, ta, wl.H, per_step / 4, cores)
+    vals, samples = [], None
+    for _ in range(args.steps):
+        r = oracle_sample(plane, ta, wl.H, per_step, cores)
+        vals.append(r["value"])
+        samples = r["sample"]
+    v = statistics.median(vals)
+    pts = wl.n_templates * wl.n_bins
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": pts / v * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": wl.name},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": samples},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ---- our arm ------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1805_12258_gb300 import build as hsbuild
+    from paper_1805_12258_gb300 import hs, synth
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    hsbuild.build()
+
+    wl = workload(args.workload)
+    if rank:
+        wl.seed += 1000 * rank  # each rank sums its own plane (independent beams)
+    nt, n, H = wl.n_templates, wl.n_bins, wl.H
+    es = 4 if args.dtype == "f32" else 2
+    host32 = torch.empty((nt, n), dtype=torch.float32, pin_memory=True)
+    synth.make_plane(wl, out=host32.numpy())
+    plane_np = host32.numpy()
+    ta = synth.thresholds(wl.p_fa, H, nt)
+    if args.dtype == "f32":
+        host = host32
+    else:
+        host = host32.to(torch.bfloat16).pin_memory()
+    fop = host.cuda()
+    fop32 = fop if args.dtype == "f32" else host32.cuda()
+    cands = hs.CandBuffer(1 << 20)
+    plan = hs.Plan(nt, n, H, ta, dtype=args.dtype, order=args.order, tile_bins=args.tile_bins)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.run(fop, cands, stream, fop_f32=None if args.dtype == "f32" else fop32)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    st, n_cand = cands.sync(stream)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    plan.set_timing(True)
+    plan.kernel_time()  # clear
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)  # sampler warm-up
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches_before = 0
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+        launches_before += hs.hs_last_launch_count()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    elapsed_ms = e0.elapsed_time(e1)
+    kern_ms, kern_n = plan.kernel_time()
+    plan.set_timing(False)
+    t = torch.tensor([elapsed_ms], device="cuda")
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    elapsed_ms = float(t.item())
+    st, n_cand = cands.sync(stream)
+
+    points = nt * n
+    value = points * ws * args.steps / (elapsed_ms / 1e3)
+    ms_per_step = elapsed_ms / args.steps
+    mean_kernel_s = kern_ms / max(kern_n, 1) / 1e3
+    algo_bytes = nt * n * es + H * nt * 4 + 16 * n_cand + 8
+    if args.dtype != "f32":
+        algo_bytes += 0  # rechecks read only near-threshold points of the FP32 copy
+    peak, peak_kind = peaks()
+    achieved_gbs = algo_bytes / mean_kernel_s / 1e9
+    kname = f"staged {nt}x{n} H={H} {args.dtype} tb={plan.tile_bins}"
+
+    # e2e through hs_run_host: pinned host plane -> device, sum, records -> host
+    e2e = None
+    if args.e2e_steps > 0:
+        dev = torch.empty_like(host, device="cuda")
+        out = np.zeros(1 << 16, hs.CAND_DTYPE)
+        plan.run_host(host, dev, cands, out, stream)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        d2h = 0
+        for _ in range(args.e2e_steps):
+            _, ne = plan.run_host(host, dev, cands, out, stream)
+            d2h += 8 + 16 * min(ne, len(out))
+        te = time.perf_counter() - t0
+        tt = torch.tensor([te], device="cuda")
+        if ws > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        te = float(tt.item())
+        e2e = {"value": points * ws * args.e2e_steps / te, "unit": UNIT,
+               "h2d_bytes_per_step": nt * n * es, "d2h_bytes_per_step": d2h // args.e2e_steps,
+               "ms_per_step": te * 1e3 / args.e2e_steps}
+        del dev
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = oracle_sample(plane_np, ta, H, args.cpu_seconds, host_cores())
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+            "config": {"workload": wl.name, "n_templates": nt, "n_bins": n, "H": H,
+                       "p_fa": wl.p_fa, "kernel": plan.kernel, "tile_bins": plan.tile_bins,
+                       "order": args.order, "candidates": n_cand,
+                       "l2": f"plane {nt * n * es / 1e6:.0f} MB > {L2_BYTES / 1e6:.0f} MB L2: "
+                             "inputs larger than L2, no flush",
+                       "parallelism": f"{ws} independent planes (one per GPU)"},
+            "level_sums_per_s": value * H,
+            "effective_hbm_gbs": algo_bytes * ws * args.steps / (elapsed_ms / 1e3) / 1e9,
+            "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peak,
+                         "unit": "GB/s", "frac": achieved_gbs / peak,
+                         "traffic": profiled_traffic(kname),
+                         "peak_kind": f"{peak_kind} copy bandwidth",
+                         "kernel": kname, "algo_bytes_per_launch": algo_bytes,
+                         "mean_kernel_us": mean_kernel_s * 1e6,
+                         "frac_of_8tbs": algo_bytes / mean_kernel_s / 8e12},
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
+            "gpu_launches": launches_before, "status": hs.hs_status_str(st),
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,190 @@
+/*
+ * hs.h -- C ABI of libhs, a GB300 (sm_103a) harmonic summer for
+ * Fourier-domain acceleration search.
+ *
+ * The operation (Wang, Thiagaraj & Sinnen, arXiv 1805.12258, Section III):
+ * the filter-output plane (FOP) holds n_templates rows of detected power,
+ * indexed by a signed template z in [-Z, Z] (Z = (n_templates-1)/2, row
+ * r = z + Z), times n_bins frequency bins f.  For every point and every
+ * harmonic level k = 1..H the library forms
+ *
+ *     HP_k(z, f) = sum_{m=1..k} FOP(rho(z, m), floor(f / m))        (Eq. 1-2)
+ *
+ * (the stretch planes SP_m of Eq. 1 summed cumulatively as in Eq. 2), tests
+ * HP_k(z, f) > TA(k, z) against a per-level, per-row threshold, and appends
+ * every hit to a candidate list.  Harmonic planes are never stored: all H
+ * levels of a point are formed together and discarded after the test, the
+ * MultipleHP loop order of Algorithm 2.
+ *
+ * rho(z, m) is sign(z) * floor(|z| / m) by default (the two template groups
+ * stretched separately, Section III); HS_ZROUND_FLOOR selects floor(z / m).
+ * HS_INDEX_HFRAC selects the harmonic-fraction sum
+ * S_k(z, f) = sum_{h=1..k} FOP(rho(z*h/k), floor(f*h/k)) instead (not in the
+ * paper; offered so that both readings of "sum over harmonics" exist).
+ *
+ * Conventions.
+ *  - Device pointers are CUDA device (or managed) addresses on the current
+ *    device.  Host pointers are ordinary CPU memory.
+ *  - A stream argument is a cudaStream_t (NULL = legacy default stream).
+ *  - Every call returns an hs_status; hs_last_error() gives a message for the
+ *    last failure on the calling thread.
+ *  - Calls that take a stream only enqueue work; they do not synchronise
+ *    unless their comment says so.  Errors that only the device can see (a
+ *    wait that timed out) are reported by hs_cand_sync().
+ */
+#ifndef HS_H
+#define HS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define HS_API __attribute__((visibility("default")))
+#else
+#define HS_API
+#endif
+
+typedef struct CUstream_st *hs_stream_t; /* same type as cudaStream_t */
+
+typedef enum {
+    HS_OK = 0,
+    HS_ERR_INVALID = 1,     /* bad argument (shape, pointer, alignment, option) */
+    HS_ERR_CUDA = 2,        /* a CUDA runtime/driver call failed */
+    HS_ERR_OOM = 3,         /* device or host allocation failed */
+    HS_ERR_OVERFLOW = 4,    /* more candidates than the buffer holds */
+    HS_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
+    HS_ERR_UNSUPPORTED = 6  /* valid request this build does not implement */
+} hs_status;
+
+typedef enum { HS_F32 = 0, HS_BF16 = 1, HS_F16 = 2 } hs_dtype;
+typedef enum { HS_INDEX_STRETCH = 0, HS_INDEX_HFRAC = 1 } hs_index;
+typedef enum { HS_ZROUND_SYMMETRIC = 0, HS_ZROUND_FLOOR = 1 } hs_zround;
+typedef enum { HS_KERNEL_AUTO = 0, HS_KERNEL_GENERIC = 1, HS_KERNEL_STAGED = 2 } hs_kernel;
+
+/* Plan options.  Zero-initialise for the defaults. */
+typedef struct {
+    int dtype;      /* hs_dtype of the stored plane (default HS_F32) */
+    int index;      /* hs_index (default HS_INDEX_STRETCH, Eq. 1-2) */
+    int zround;     /* hs_zround (default HS_ZROUND_SYMMETRIC) */
+    int kernel;     /* hs_kernel: AUTO picks the staged kernel when it applies */
+    int tile_bins;  /* bins per CTA of the staged kernel: 0 = default */
+    int order;      /* tile order: 0 = default, 1 = linear, 2 = octave-interleaved */
+    int reserved[2];
+} hs_options;
+
+/* Candidate record flags */
+#define HS_FLAG_LOWP 0x1u /* decided on a 16-bit plane without an FP32 recheck */
+#define HS_FLAG_NEAR 0x2u /* ... and within the 16-bit error band of its threshold */
+
+/* One candidate, 16 bytes.  Section III packs (filter, plane, bin, amplitude)
+ * into two 32-bit words; that packing cannot hold H = 16 with 2^22 bins, so
+ * the record is widened (hs_pack_paper() gives the paper's form when it fits). */
+typedef struct {
+    uint32_t bin;      /* f */
+    int16_t z;         /* signed template index */
+    uint8_t k;         /* harmonic level, 1..H */
+    uint8_t flags;     /* HS_FLAG_* */
+    float power;       /* HP_k(z, f) as computed in FP32 */
+    uint32_t reserved; /* 0 */
+} hs_cand;
+
+/* Caller-owned device candidate buffer.
+ *  records : device array of `capacity` records.
+ *  count   : device array of 2 uint32: [0] = number of candidates found
+ *            (may exceed capacity; records beyond it are dropped),
+ *            [1] = device status (HS_OK or HS_ERR_TIMEOUT).
+ * hs_run resets both words on its stream before its kernel. */
+typedef struct {
+    hs_cand *records;
+    uint32_t *count;
+    uint32_t capacity;
+} hs_cand_buf;
+
+typedef struct hs_plan hs_plan;
+
+/* Create a plan (Section III, Table I parameters N_temp, N_chan, N_hp).
+ *  n_templates : odd, 1..32767.   n_bins : 1..2^31-1.   H : 1..32.
+ *  thresholds  : host array TA[H][n_templates] (level-major, binary32, all
+ *                finite); copied, the caller keeps ownership.
+ *  opt         : NULL for defaults.
+ * Allocates the plan's device tables on the current device.
+ * Errors: HS_ERR_INVALID, HS_ERR_UNSUPPORTED (HFRAC with H > 32),
+ *         HS_ERR_OOM, HS_ERR_CUDA. */
+HS_API hs_status hs_plan_create(hs_plan **out, int n_templates, int64_t n_bins, int H,
+                         const float *thresholds, const hs_options *opt);
+
+/* Enqueue harmonic summing + detection of one plane on `stream`.
+ *  fop   : device plane [n_templates][n_bins], row-major, plan dtype,
+ *          16-byte aligned; borrowed until the stream passes the kernel.
+ *  cands : caller-owned buffer (see hs_cand_buf).
+ * A plan may serve several streams at once if each run has its own cands.
+ * Errors: HS_ERR_INVALID (null/misaligned pointers), HS_ERR_CUDA. */
+HS_API hs_status hs_run(hs_plan *plan, const void *fop, hs_stream_t stream,
+                 const hs_cand_buf *cands);
+
+/* As hs_run for a 16-bit plan, with an optional FP32 copy of the same plane.
+ * When fop_f32 is given, every point whose 16-bit level sum could lie on
+ * either side of its threshold is re-evaluated from the FP32 copy with the
+ * FP32 path's arithmetic, so the candidate set (and each record) equals
+ * hs_run on the FP32 plane.  When fop_f32 is NULL the 16-bit sums decide and
+ * records carry HS_FLAG_LOWP (and HS_FLAG_NEAR inside the error band).
+ * For an FP32 plan fop_f32 must be NULL. */
+HS_API hs_status hs_run_checked(hs_plan *plan, const void *fop, const float *fop_f32,
+                         hs_stream_t stream, const hs_cand_buf *cands);
+
+/* Synchronise `stream`, read the candidate count and device status.
+ *  n_out : receives the number of candidates found (the true count).
+ * Returns HS_ERR_TIMEOUT if a device wait gave up, HS_ERR_OVERFLOW if
+ * *n_out > capacity (the first `capacity` records are valid), else HS_OK. */
+HS_API hs_status hs_cand_sync(const hs_cand_buf *cands, hs_stream_t stream, uint32_t *n_out);
+
+/* End-to-end call on host memory: copies fop_host (the plane, plan dtype,
+ * ideally page-locked) to fop_dev in frequency chunks and overlaps each copy
+ * with the summing of the bins it completes, then copies the candidates back.
+ * Synchronous.
+ *  fop_dev      : device scratch plane of the same size (caller-owned).
+ *  cands        : device candidate buffer (caller-owned).
+ *  host_records : host array of host_capacity records (may be NULL if 0).
+ *  n_out        : true candidate count.
+ * Errors as hs_run and hs_cand_sync. */
+HS_API hs_status hs_run_host(hs_plan *plan, const void *fop_host, void *fop_dev,
+                      const hs_cand_buf *cands, hs_cand *host_records,
+                      uint32_t host_capacity, hs_stream_t stream, uint32_t *n_out);
+
+/* Destroy a plan (NULL is accepted).  Synchronises the device first. */
+HS_API hs_status hs_plan_destroy(hs_plan *plan);
+
+/* Which kernel a plan runs: 1 = generic, 2 = staged (TMA). */
+HS_API int hs_plan_kernel(const hs_plan *plan);
+
+/* Bins per CTA of the plan's kernel. */
+HS_API int hs_plan_tile_bins(const hs_plan *plan);
+
+/* Kernel timing for profiling.  While enabled, every kernel launch of the plan
+ * is bracketed by CUDA events on its stream (kernels only: not the counter
+ * reset or copies).  hs_plan_kernel_time waits for the recorded launches,
+ * returns their summed device time in milliseconds and their number, and
+ * clears the record.  Errors: HS_ERR_INVALID (null plan), HS_ERR_CUDA. */
+HS_API hs_status hs_plan_set_timing(hs_plan *plan, int enable);
+HS_API hs_status hs_plan_kernel_time(hs_plan *plan, double *total_ms, int *launches);
+
+/* Kernels launched by the last hs_run* call on this thread. */
+HS_API int hs_last_launch_count(void);
+
+/* The paper's packed candidate form (Section III): CL1 = F*2^24 + H*2^21 + B,
+ * CL2 = A, with F the row r = z + Z (7 bits), H the 0-based level (3 bits),
+ * B the bin (21 bits).  HS_ERR_INVALID when a field does not fit. */
+HS_API hs_status hs_pack_paper(const hs_cand *c, int n_templates, uint32_t *cl1, float *cl2);
+
+HS_API const char *hs_status_str(hs_status s);
+HS_API const char *hs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HS_H */

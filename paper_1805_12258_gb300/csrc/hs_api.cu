@@ -1,0 +1,548 @@
+// hs_api.cu -- host implementation of the C ABI declared in include/hs.h:
+// plan creation (validation, device threshold table, prefilter thresholds,
+// tile order), kernel selection, TMA descriptor encoding, the end-to-end
+// host-memory call and status reporting.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cudaTypedefs.h>
+
+#include "hs_internal.h"
+
+using namespace hs;
+
+struct hs_plan {
+    int nt = 0;
+    long long n = 0;
+    int H = 0;
+    hs_options opt{};
+    int device = 0;
+    int kernel = HS_KERNEL_GENERIC;
+    int tb = 128;
+    int groups = 0;
+    int n_tiles = 0;
+    float delta = 0.f;     // relative error bound of 16-bit storage
+    float band_abs = 0.f;  // absolute error bound (FP16 subnormals)
+    std::vector<float> ta;   // [H][nt]
+    std::vector<float> tmin; // [groups]: min over rows and the group's levels
+    float *d_ta = nullptr;
+    uint32_t *d_order = nullptr;
+    std::mutex mu;                 // guards the descriptor cache and streams
+    const void *map_ptr = nullptr; // plane the cached descriptors encode
+    CUtensorMap maps[kMaxStagedH];
+    cudaStream_t copy_stream = nullptr;
+    std::vector<cudaEvent_t> chunk_events;
+    bool timing = false;             // bracket kernel launches with events
+    std::vector<cudaEvent_t> tev;    // event pool: (start, stop) pairs
+    size_t tev_used = 0;             // events recorded since the last query
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+thread_local int g_last_launches = 0;
+
+hs_status fail(hs_status s, const std::string &msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+hs_status cuda_fail(cudaError_t e, const char *what)
+{
+    g_last_error = std::string(what) + ": " + cudaGetErrorName(e) + " (" +
+                   cudaGetErrorString(e) + ")";
+    return e == cudaErrorMemoryAllocation ? HS_ERR_OOM : HS_ERR_CUDA;
+}
+
+size_t elem_size(int dtype) { return dtype == HS_F32 ? 4 : 2; }
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// One 2-D descriptor per stretch factor m over the plane [nt][n].
+hs_status encode_maps(hs_plan *p, const void *fop)
+{
+    if (p->map_ptr == fop)
+        return HS_OK;
+    auto fn = encode_fn();
+    if (!fn)
+        return fail(HS_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const StagedShape sh{p->nt, p->H, p->tb, p->opt.dtype};
+    const CUtensorMapDataType dt = p->opt.dtype == HS_F32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : p->opt.dtype == HS_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                             : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    const size_t es = elem_size(p->opt.dtype);
+    for (int m = 1; m <= p->H; ++m) {
+        int w = 0, rows = 0;
+        staged_box(sh, m, &w, &rows);
+        cuuint64_t dims[2] = {(cuuint64_t)p->n, (cuuint64_t)p->nt};
+        cuuint64_t strides[1] = {(cuuint64_t)p->n * es};
+        cuuint32_t box[2] = {(cuuint32_t)w, (cuuint32_t)rows};
+        cuuint32_t estr[2] = {1, 1};
+        CUresult r = fn(&p->maps[m - 1], dt, 2, const_cast<void *>(fop), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            p->map_ptr = nullptr;
+            char buf[128];
+            std::snprintf(buf, sizeof buf, "cuTensorMapEncodeTiled failed (%d) for m=%d", (int)r, m);
+            return fail(HS_ERR_CUDA, buf);
+        }
+    }
+    p->map_ptr = fop;
+    return HS_OK;
+}
+
+// Tile order: linear, or octave-interleaved (tiles sorted by the mantissa of
+// their index, then by octave) so that the tiles reading a span at f/2, f/4,
+// ... run close in time to the tile that reads it at f.
+std::vector<uint32_t> tile_order(int n_tiles, int kind)
+{
+    std::vector<uint32_t> o(n_tiles);
+    for (int t = 0; t < n_tiles; ++t)
+        o[t] = (uint32_t)t;
+    if (kind == 2) {
+        auto key = [](uint32_t t) {
+            if (t == 0)
+                return std::make_pair(1.0, -1);
+            int e = 31 - __builtin_clz(t);
+            return std::make_pair((double)t / (double)(1u << e), e);
+        };
+        std::stable_sort(o.begin(), o.end(),
+                         [&](uint32_t a, uint32_t b) { return key(a) < key(b); });
+    }
+    return o;
+}
+
+hs_status check_cands(const hs_cand_buf *c)
+{
+    if (!c || !c->count)
+        return fail(HS_ERR_INVALID, "candidate buffer or its count pointer is null");
+    if (c->capacity > 0 && !c->records)
+        return fail(HS_ERR_INVALID, "candidate records pointer is null with capacity > 0");
+    if (reinterpret_cast<uintptr_t>(c->records) % 16 != 0)
+        return fail(HS_ERR_INVALID, "candidate records must be 16-byte aligned");
+    return HS_OK;
+}
+
+// Launch the plan's kernel over bins [f_lo, f_hi) (tile-aligned for the
+// staged kernel unless f_hi == n).  Linear order is used for partial ranges.
+hs_status launch_range(hs_plan *p, const void *fop, const float *fop32, cudaStream_t s,
+                       const hs_cand_buf *c, long long f_lo, long long f_hi, bool full)
+{
+    cudaError_t e;
+    cudaEvent_t ev_stop = nullptr;
+    if (p->timing) {
+        while (p->tev.size() < p->tev_used + 2) {
+            cudaEvent_t ev;
+            e = cudaEventCreate(&ev);
+            if (e != cudaSuccess)
+                return cuda_fail(e, "cudaEventCreate (timing)");
+            p->tev.push_back(ev);
+        }
+        e = cudaEventRecord(p->tev[p->tev_used], s);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "cudaEventRecord (timing)");
+        ev_stop = p->tev[p->tev_used + 1];
+        p->tev_used += 2;
+    }
+    if (p->kernel == HS_KERNEL_STAGED) {
+        hs_status st = encode_maps(p, fop);
+        if (st != HS_OK)
+            return st;
+        StagedLaunch L{};
+        L.sh = StagedShape{p->nt, p->H, p->tb, p->opt.dtype};
+        L.maps = p->maps;
+        L.tmin_host = p->tmin.data();
+        L.ta = p->d_ta;
+        L.fop32 = fop32;
+        L.order = full ? p->d_order : nullptr;
+        L.delta = p->delta;
+        L.band_abs = p->band_abs;
+        L.rec = c->records;
+        L.counters = c->count;
+        L.cap = c->capacity;
+        L.n = p->n;
+        L.tile_lo = (int)(f_lo / p->tb);
+        L.tile_hi = (int)((f_hi + p->tb - 1) / p->tb);
+        e = launch_staged(L, s);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "staged kernel launch");
+    } else {
+        GenericArgs a{};
+        a.fop = fop;
+        a.fop32 = fop32;
+        a.dtype = p->opt.dtype;
+        a.nt = p->nt;
+        a.n = p->n;
+        a.H = p->H;
+        a.index = p->opt.index;
+        a.zround = p->opt.zround;
+        a.ta = p->d_ta;
+        a.delta = p->delta;
+        a.band_abs = p->band_abs;
+        a.rec = c->records;
+        a.counters = c->count;
+        a.cap = c->capacity;
+        a.f_lo = f_lo;
+        a.f_hi = f_hi;
+        e = launch_generic(a, s);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "generic kernel launch");
+    }
+    ++g_last_launches;
+    if (ev_stop) {
+        e = cudaEventRecord(ev_stop, s);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "cudaEventRecord (timing)");
+    }
+    return HS_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+const char *hs_status_str(hs_status s)
+{
+    switch (s) {
+    case HS_OK: return "ok";
+    case HS_ERR_INVALID: return "invalid argument";
+    case HS_ERR_CUDA: return "CUDA error";
+    case HS_ERR_OOM: return "out of memory";
+    case HS_ERR_OVERFLOW: return "candidate buffer overflow";
+    case HS_ERR_TIMEOUT: return "device wait timed out";
+    case HS_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char *hs_last_error(void) { return g_last_error.c_str(); }
+
+int hs_last_launch_count(void) { return g_last_launches; }
+
+hs_status hs_plan_create(hs_plan **out, int n_templates, int64_t n_bins, int H,
+                         const float *thresholds, const hs_options *opt)
+{
+    if (!out)
+        return fail(HS_ERR_INVALID, "out is null");
+    *out = nullptr;
+    hs_options o{};
+    if (opt)
+        o = *opt;
+    if (n_templates < 1 || n_templates % 2 == 0 || n_templates > 32767)
+        return fail(HS_ERR_INVALID, "n_templates must be odd and in [1, 32767]");
+    if (n_bins < 1 || n_bins > 0x7fffffffLL)
+        return fail(HS_ERR_INVALID, "n_bins must be in [1, 2^31-1]");
+    if (H < 1 || H > 32)
+        return fail(HS_ERR_INVALID, "H must be in [1, 32]");
+    if (!thresholds)
+        return fail(HS_ERR_INVALID, "thresholds is null");
+    if (o.dtype < HS_F32 || o.dtype > HS_F16 || o.index < 0 || o.index > 1 || o.zround < 0 ||
+        o.zround > 1 || o.kernel < 0 || o.kernel > 2 || o.order < 0 || o.order > 2 ||
+        o.tile_bins < 0)
+        return fail(HS_ERR_INVALID, "unknown option value");
+    for (long long i = 0; i < (long long)H * n_templates; ++i)
+        if (!std::isfinite(thresholds[i]))
+            return fail(HS_ERR_INVALID, "thresholds must be finite");
+
+    hs_plan *p = new (std::nothrow) hs_plan();
+    if (!p)
+        return fail(HS_ERR_OOM, "host allocation of the plan failed");
+    p->nt = n_templates;
+    p->n = n_bins;
+    p->H = H;
+    p->opt = o;
+    cudaGetDevice(&p->device);
+    p->ta.assign(thresholds, thresholds + (size_t)H * n_templates);
+    if (o.dtype == HS_BF16)
+        p->delta = (float)((std::ldexp(1.0, -8) + H * std::ldexp(1.0, -22)) * 1.01);
+    else if (o.dtype == HS_F16) {
+        p->delta = (float)((std::ldexp(1.0, -11) + H * std::ldexp(1.0, -22)) * 1.01);
+        p->band_abs = (float)(H * std::ldexp(1.0, -24));
+    }
+
+    // kernel choice: the staged kernel needs a compiled shape, the paper's
+    // index map with symmetric rounding, and 16-byte aligned rows for TMA
+    const size_t es = elem_size(o.dtype);
+    p->tb = o.tile_bins ? o.tile_bins : 128;
+    const StagedShape sh{n_templates, H, p->tb, o.dtype};
+    const bool staged_ok = staged_available(sh) && o.index == HS_INDEX_STRETCH &&
+                           o.zround == HS_ZROUND_SYMMETRIC && (n_bins * es) % 16 == 0;
+    if (o.kernel == HS_KERNEL_STAGED && !staged_ok) {
+        delete p;
+        return fail(HS_ERR_UNSUPPORTED, "no staged kernel for this shape/options "
+                                        "(compiled: 85x16 and 21x8, stretch, symmetric, "
+                                        "rows a multiple of 16 bytes)");
+    }
+    if (o.kernel == HS_KERNEL_GENERIC || !staged_ok) {
+        p->kernel = HS_KERNEL_GENERIC;
+        p->tb = 128;
+    } else {
+        p->kernel = HS_KERNEL_STAGED;
+    }
+
+    cudaError_t e = cudaMalloc(&p->d_ta, sizeof(float) * p->ta.size());
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_fail(e, "cudaMalloc thresholds");
+    }
+    e = cudaMemcpy(p->d_ta, p->ta.data(), sizeof(float) * p->ta.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        hs_plan_destroy(p);
+        return cuda_fail(e, "cudaMemcpy thresholds");
+    }
+
+    if (p->kernel == HS_KERNEL_STAGED) {
+        int ends[kMaxGroups];
+        p->groups = staged_groups(H, ends);
+        p->tmin.assign((size_t)p->groups, 0.f);
+        int a = 1;
+        for (int g = 0; g < p->groups; ++g) {
+            double t = INFINITY;
+            for (int k = a; k <= ends[g]; ++k)
+                for (int r = 0; r < n_templates; ++r)
+                    t = std::min(t, (double)p->ta[(size_t)(k - 1) * n_templates + r]);
+            // exact condition s (1 + delta) > t - band_abs, rounded down
+            double lowered = (t - p->band_abs) / (1.0 + p->delta);
+            float lf = (float)lowered;
+            if ((double)lf > lowered)
+                lf = std::nextafter(lf, -INFINITY);
+            p->tmin[g] = p->delta == 0.f ? (float)t : lf;
+            a = ends[g] + 1;
+        }
+        p->n_tiles = (int)((n_bins + p->tb - 1) / p->tb);
+        const int kind = o.order == 0 ? 1 : o.order;
+        std::vector<uint32_t> ord = tile_order(p->n_tiles, kind);
+        e = cudaMalloc(&p->d_order, sizeof(uint32_t) * ord.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(p->d_order, ord.data(), sizeof(uint32_t) * ord.size(),
+                           cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            hs_plan_destroy(p);
+            return cuda_fail(e, "tile order table");
+        }
+    }
+    *out = p;
+    return HS_OK;
+}
+
+int hs_plan_kernel(const hs_plan *p) { return p ? p->kernel : 0; }
+
+int hs_plan_tile_bins(const hs_plan *p) { return p ? p->tb : 0; }
+
+hs_status hs_run_checked(hs_plan *p, const void *fop, const float *fop32, hs_stream_t stream,
+                         const hs_cand_buf *cands)
+{
+    g_last_launches = 0;
+    if (!p)
+        return fail(HS_ERR_INVALID, "plan is null");
+    if (!fop || reinterpret_cast<uintptr_t>(fop) % 16 != 0)
+        return fail(HS_ERR_INVALID, "plane pointer must be non-null and 16-byte aligned");
+    if (fop32 && p->opt.dtype == HS_F32)
+        return fail(HS_ERR_INVALID, "an FP32 plan takes no recheck copy");
+    if (fop32 && reinterpret_cast<uintptr_t>(fop32) % 16 != 0)
+        return fail(HS_ERR_INVALID, "recheck copy must be 16-byte aligned");
+    hs_status st = check_cands(cands);
+    if (st != HS_OK)
+        return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(cands->count, 0, 2 * sizeof(uint32_t), s);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaMemsetAsync counters");
+    std::lock_guard<std::mutex> lk(p->mu);
+    return launch_range(p, fop, fop32, s, cands, 0, p->n, true);
+}
+
+hs_status hs_run(hs_plan *p, const void *fop, hs_stream_t stream, const hs_cand_buf *cands)
+{
+    return hs_run_checked(p, fop, nullptr, stream, cands);
+}
+
+hs_status hs_cand_sync(const hs_cand_buf *cands, hs_stream_t stream, uint32_t *n_out)
+{
+    hs_status st = check_cands(cands);
+    if (st != HS_OK)
+        return st;
+    uint32_t h[2] = {0, 0};
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(h, cands->count, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "reading candidate count");
+    if (n_out)
+        *n_out = h[0];
+    if (h[1] != 0)
+        return fail((hs_status)h[1], "device reported a failed bounded wait");
+    if (h[0] > cands->capacity)
+        return fail(HS_ERR_OVERFLOW, "more candidates than the buffer capacity");
+    return HS_OK;
+}
+
+hs_status hs_run_host(hs_plan *p, const void *fop_host, void *fop_dev, const hs_cand_buf *cands,
+                      hs_cand *host_records, uint32_t host_capacity, hs_stream_t stream,
+                      uint32_t *n_out)
+{
+    g_last_launches = 0;
+    if (!p || !fop_host || !fop_dev)
+        return fail(HS_ERR_INVALID, "plan, host plane and device plane must be non-null");
+    if (reinterpret_cast<uintptr_t>(fop_dev) % 16 != 0)
+        return fail(HS_ERR_INVALID, "device plane must be 16-byte aligned");
+    if (host_capacity > 0 && !host_records)
+        return fail(HS_ERR_INVALID, "host_records is null with host_capacity > 0");
+    hs_status st = check_cands(cands);
+    if (st != HS_OK)
+        return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t es = elem_size(p->opt.dtype);
+    const int n_chunks = 8;
+    {
+        std::lock_guard<std::mutex> lk(p->mu);
+        cudaError_t e = cudaSuccess;
+        if (!p->copy_stream)
+            e = cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking);
+        while (e == cudaSuccess && (int)p->chunk_events.size() < n_chunks + 1) {
+            cudaEvent_t ev;
+            e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e == cudaSuccess)
+                p->chunk_events.push_back(ev);
+        }
+        if (e != cudaSuccess)
+            return cuda_fail(e, "creating copy stream/events");
+        // the copy stream starts after work already queued on `stream`
+        e = cudaEventRecord(p->chunk_events[n_chunks], s);
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(p->copy_stream, p->chunk_events[n_chunks], 0);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(cands->count, 0, 2 * sizeof(uint32_t), s);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "ordering the copy stream");
+        // chunk edges: tile-aligned so each chunk's outputs need only bins
+        // already copied (every source bin floor(f/m) <= f)
+        const long long unit = p->kernel == HS_KERNEL_STAGED ? p->tb : 128;
+        const long long units = (p->n + unit - 1) / unit;
+        long long prev = 0;
+        for (int c = 0; c < n_chunks; ++c) {
+            long long hi = (c == n_chunks - 1) ? p->n : std::min(p->n, units * (c + 1) / n_chunks * unit);
+            if (hi <= prev)
+                continue;
+            const size_t off = (size_t)prev * es, width = (size_t)(hi - prev) * es,
+                         pitch = (size_t)p->n * es;
+            e = cudaMemcpy2DAsync(static_cast<char *>(fop_dev) + off, pitch,
+                                  static_cast<const char *>(fop_host) + off, pitch, width,
+                                  (size_t)p->nt, cudaMemcpyHostToDevice, p->copy_stream);
+            if (e == cudaSuccess)
+                e = cudaEventRecord(p->chunk_events[c], p->copy_stream);
+            if (e == cudaSuccess)
+                e = cudaStreamWaitEvent(s, p->chunk_events[c], 0);
+            if (e != cudaSuccess)
+                return cuda_fail(e, "host-to-device chunk copy");
+            st = launch_range(p, fop_dev, nullptr, s, cands, prev, hi, false);
+            if (st != HS_OK)
+                return st;
+            prev = hi;
+        }
+    }
+    uint32_t n = 0;
+    hs_status sync = hs_cand_sync(cands, stream, &n);
+    if (sync != HS_OK && sync != HS_ERR_OVERFLOW)
+        return sync;
+    if (n_out)
+        *n_out = n;
+    const uint32_t ncopy = std::min(std::min(n, cands->capacity), host_capacity);
+    if (ncopy > 0) {
+        cudaError_t e = cudaMemcpyAsync(host_records, cands->records, sizeof(hs_cand) * ncopy,
+                                        cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "device-to-host candidate copy");
+    }
+    if (sync == HS_OK && n > host_capacity)
+        return fail(HS_ERR_OVERFLOW, "more candidates than the host buffer capacity");
+    return sync;
+}
+
+hs_status hs_plan_set_timing(hs_plan *p, int enable)
+{
+    if (!p)
+        return fail(HS_ERR_INVALID, "plan is null");
+    std::lock_guard<std::mutex> lk(p->mu);
+    p->timing = enable != 0;
+    return HS_OK;
+}
+
+hs_status hs_plan_kernel_time(hs_plan *p, double *total_ms, int *launches)
+{
+    if (!p)
+        return fail(HS_ERR_INVALID, "plan is null");
+    std::lock_guard<std::mutex> lk(p->mu);
+    double total = 0.0;
+    for (size_t i = 0; i + 1 < p->tev_used; i += 2) {
+        cudaError_t e = cudaEventSynchronize(p->tev[i + 1]);
+        float ms = 0.f;
+        if (e == cudaSuccess)
+            e = cudaEventElapsedTime(&ms, p->tev[i], p->tev[i + 1]);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "reading kernel timing events");
+        total += ms;
+    }
+    if (total_ms)
+        *total_ms = total;
+    if (launches)
+        *launches = (int)(p->tev_used / 2);
+    p->tev_used = 0;
+    return HS_OK;
+}
+
+hs_status hs_plan_destroy(hs_plan *p)
+{
+    if (!p)
+        return HS_OK;
+    cudaDeviceSynchronize();
+    cudaFree(p->d_ta);
+    cudaFree(p->d_order);
+    for (cudaEvent_t ev : p->tev)
+        cudaEventDestroy(ev);
+    for (cudaEvent_t ev : p->chunk_events)
+        cudaEventDestroy(ev);
+    if (p->copy_stream)
+        cudaStreamDestroy(p->copy_stream);
+    delete p;
+    return HS_OK;
+}
+
+hs_status hs_pack_paper(const hs_cand *c, int n_templates, uint32_t *cl1, float *cl2)
+{
+    if (!c || !cl1 || !cl2 || n_templates < 1 || n_templates % 2 == 0)
+        return fail(HS_ERR_INVALID, "null argument or even template count");
+    const int Z = (n_templates - 1) / 2;
+    const int r = c->z + Z;
+    if (r < 0 || r >= 128 || c->k < 1 || c->k > 8 || c->bin >= (1u << 21))
+        return fail(HS_ERR_INVALID, "field does not fit the 7+3+21-bit packing");
+    *cl1 = ((uint32_t)r << 24) | ((uint32_t)(c->k - 1) << 21) | c->bin;
+    *cl2 = c->power;
+    return HS_OK;
+}
+
+} // extern "C"

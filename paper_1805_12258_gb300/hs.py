@@ -1,0 +1,295 @@
+"""Thin ctypes binding of libhs (include/hs.h).
+
+The functions named after the C ABI (hs_plan_create, hs_run, ...) only
+marshal arguments; every step of harmonic summing runs in the library's CUDA
+kernels.  PyTorch supplies device memory and streams.  If libhs.so is missing
+the binding raises: there is no CPU fallback.
+
+Convenience wrappers: ``Plan`` (owns an hs_plan) and ``CandBuffer`` (owns a
+device candidate buffer).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhs.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "hs.h")
+
+HS_OK, HS_ERR_INVALID, HS_ERR_CUDA, HS_ERR_OOM, HS_ERR_OVERFLOW, HS_ERR_TIMEOUT, \
+    HS_ERR_UNSUPPORTED = range(7)
+HS_F32, HS_BF16, HS_F16 = 0, 1, 2
+HS_INDEX_STRETCH, HS_INDEX_HFRAC = 0, 1
+HS_ZROUND_SYMMETRIC, HS_ZROUND_FLOOR = 0, 1
+HS_KERNEL_AUTO, HS_KERNEL_GENERIC, HS_KERNEL_STAGED = 0, 1, 2
+HS_FLAG_LOWP, HS_FLAG_NEAR = 1, 2
+
+DTYPES = {"f32": HS_F32, "bf16": HS_BF16, "f16": HS_F16}
+INDEX = {"stretch": HS_INDEX_STRETCH, "hfrac": HS_INDEX_HFRAC}
+ZROUND = {"symmetric": HS_ZROUND_SYMMETRIC, "floor": HS_ZROUND_FLOOR}
+KERNELS = {"auto": HS_KERNEL_AUTO, "generic": HS_KERNEL_GENERIC, "staged": HS_KERNEL_STAGED}
+
+CAND_DTYPE = np.dtype([("bin", "<u4"), ("z", "<i2"), ("k", "u1"), ("flags", "u1"),
+                       ("power", "<f4"), ("reserved", "<u4")])
+assert CAND_DTYPE.itemsize == 16
+
+
+class HsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class hs_options(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int), ("index", ctypes.c_int), ("zround", ctypes.c_int),
+                ("kernel", ctypes.c_int), ("tile_bins", ctypes.c_int), ("order", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
+
+
+class hs_cand(ctypes.Structure):
+    _fields_ = [("bin", ctypes.c_uint32), ("z", ctypes.c_int16), ("k", ctypes.c_uint8),
+                ("flags", ctypes.c_uint8), ("power", ctypes.c_float),
+                ("reserved", ctypes.c_uint32)]
+
+
+class hs_cand_buf(ctypes.Structure):
+    _fields_ = [("records", ctypes.c_void_p), ("count", ctypes.c_void_p),
+                ("capacity", ctypes.c_uint32)]
+
+
+_lib = None
+
+
+def header_functions() -> list:
+    """Names of the functions include/hs.h declares."""
+    with open(HEADER) as fh:
+        return re.findall(r"^HS_API\s+[\w\s\*]+?\b(hs_\w+)\s*\(", fh.read(), re.M)
+
+
+def lib():
+    """Load libhs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libhs.so not found at {LIB_PATH}; run "
+                           "`python -m paper_1805_12258_gb300.build` first")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint32
+    P = ctypes.POINTER
+    L.hs_plan_create.argtypes = [P(vp), i32, i64, i32, vp, P(hs_options)]
+    L.hs_run.argtypes = [vp, vp, vp, P(hs_cand_buf)]
+    L.hs_run_checked.argtypes = [vp, vp, vp, vp, P(hs_cand_buf)]
+    L.hs_cand_sync.argtypes = [P(hs_cand_buf), vp, P(u32)]
+    L.hs_run_host.argtypes = [vp, vp, vp, P(hs_cand_buf), vp, u32, vp, P(u32)]
+    L.hs_plan_destroy.argtypes = [vp]
+    L.hs_plan_kernel.argtypes = [vp]
+    L.hs_plan_tile_bins.argtypes = [vp]
+    L.hs_last_launch_count.argtypes = []
+    L.hs_plan_set_timing.argtypes = [vp, i32]
+    L.hs_plan_kernel_time.argtypes = [vp, P(ctypes.c_double), P(i32)]
+    L.hs_pack_paper.argtypes = [P(hs_cand), i32, P(u32), P(ctypes.c_float)]
+    L.hs_status_str.argtypes = [i32]
+    L.hs_status_str.restype = ctypes.c_char_p
+    L.hs_last_error.argtypes = []
+    L.hs_last_error.restype = ctypes.c_char_p
+    for name in ("hs_plan_create", "hs_run", "hs_run_checked", "hs_cand_sync", "hs_run_host",
+                 "hs_plan_destroy", "hs_pack_paper", "hs_plan_set_timing",
+                 "hs_plan_kernel_time"):
+        getattr(L, name).restype = i32
+    for name in ("hs_plan_kernel", "hs_plan_tile_bins", "hs_last_launch_count"):
+        getattr(L, name).restype = i32
+    _lib = L
+    return L
+
+
+def _check(status, what, ok=(HS_OK,)):
+    if status not in ok:
+        raise HsError(status, f"{what}: {lib().hs_last_error().decode()}")
+    return status
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+# ---- the C ABI, argument marshalling only ------------------------------------
+
+def hs_plan_create(n_templates, n_bins, H, thresholds, opt: hs_options | None = None):
+    """Create a plan; thresholds is a host float32 array [H][n_templates]."""
+    ta = np.ascontiguousarray(thresholds, dtype=np.float32)
+    if ta.shape != (H, n_templates):
+        raise ValueError(f"thresholds must have shape {(H, n_templates)}, got {ta.shape}")
+    out = ctypes.c_void_p()
+    _check(lib().hs_plan_create(ctypes.byref(out), n_templates, n_bins, H, ta.ctypes.data,
+                                ctypes.byref(opt) if opt is not None else None),
+           "hs_plan_create")
+    return out.value
+
+
+def hs_run(plan, fop, stream, cands: hs_cand_buf):
+    return _check(lib().hs_run(plan, _ptr(fop), _stream_handle(stream), ctypes.byref(cands)),
+                  "hs_run")
+
+
+def hs_run_checked(plan, fop, fop_f32, stream, cands: hs_cand_buf):
+    return _check(lib().hs_run_checked(plan, _ptr(fop), _ptr(fop_f32), _stream_handle(stream),
+                                       ctypes.byref(cands)), "hs_run_checked")
+
+
+def hs_cand_sync(cands: hs_cand_buf, stream):
+    """Returns (status, n_found); raises on CUDA errors and timeouts."""
+    n = ctypes.c_uint32(0)
+    st = lib().hs_cand_sync(ctypes.byref(cands), _stream_handle(stream), ctypes.byref(n))
+    _check(st, "hs_cand_sync", ok=(HS_OK, HS_ERR_OVERFLOW))
+    return st, n.value
+
+
+def hs_run_host(plan, fop_host, fop_dev, cands: hs_cand_buf, host_records, stream):
+    """Returns (status, n_found); host_records is a CAND_DTYPE numpy array."""
+    n = ctypes.c_uint32(0)
+    cap = 0 if host_records is None else len(host_records)
+    st = lib().hs_run_host(plan, _ptr(fop_host), _ptr(fop_dev), ctypes.byref(cands),
+                           _ptr(host_records) if cap else None, cap, _stream_handle(stream),
+                           ctypes.byref(n))
+    _check(st, "hs_run_host", ok=(HS_OK, HS_ERR_OVERFLOW))
+    return st, n.value
+
+
+def hs_plan_destroy(plan):
+    return _check(lib().hs_plan_destroy(plan), "hs_plan_destroy")
+
+
+def hs_pack_paper(rec, n_templates):
+    """(CL1, CL2) of one record (Section III packing)."""
+    c = hs_cand(int(rec["bin"]), int(rec["z"]), int(rec["k"]), int(rec["flags"]),
+                float(rec["power"]), 0)
+    cl1, cl2 = ctypes.c_uint32(), ctypes.c_float()
+    _check(lib().hs_pack_paper(ctypes.byref(c), n_templates, ctypes.byref(cl1),
+                               ctypes.byref(cl2)), "hs_pack_paper")
+    return cl1.value, cl2.value
+
+
+def hs_plan_set_timing(plan, enable):
+    return _check(lib().hs_plan_set_timing(plan, int(bool(enable))), "hs_plan_set_timing")
+
+
+def hs_plan_kernel_time(plan):
+    """(summed kernel milliseconds, launches) since the last query."""
+    ms, n = ctypes.c_double(0.0), ctypes.c_int(0)
+    _check(lib().hs_plan_kernel_time(plan, ctypes.byref(ms), ctypes.byref(n)),
+           "hs_plan_kernel_time")
+    return ms.value, n.value
+
+
+def hs_status_str(s):
+    return lib().hs_status_str(s).decode()
+
+
+def hs_last_launch_count():
+    return lib().hs_last_launch_count()
+
+
+# ---- convenience wrappers ------------------------------------------------------
+
+class CandBuffer:
+    """Device candidate buffer: `capacity` 16-byte records + 2 counters."""
+
+    def __init__(self, capacity: int, device="cuda"):
+        import torch
+        self.capacity = int(capacity)
+        self.records = torch.empty(max(1, self.capacity) * 16, dtype=torch.uint8, device=device)
+        self.counters = torch.zeros(4, dtype=torch.int32, device=device)
+        self.c = hs_cand_buf(self.records.data_ptr(), self.counters.data_ptr(), self.capacity)
+
+    def sync(self, stream=None):
+        """(status, n_found) after the stream drains."""
+        return hs_cand_sync(self.c, stream)
+
+    def to_numpy(self, n: int) -> np.ndarray:
+        n = min(int(n), self.capacity)
+        raw = self.records[: n * 16].cpu().numpy()
+        return raw.view(CAND_DTYPE).copy()
+
+    def fetch(self, stream=None):
+        """Sync and return (records sorted by (k, z, bin), n_found, status)."""
+        st, n = self.sync(stream)
+        return sort_records(self.to_numpy(n)), n, st
+
+
+def sort_records(r: np.ndarray) -> np.ndarray:
+    if len(r) == 0:
+        return r
+    return r[np.lexsort((r["bin"], r["z"], r["k"]))]
+
+
+class Plan:
+    """An hs_plan for one plane shape, threshold table and option set."""
+
+    def __init__(self, n_templates, n_bins, H, thresholds, *, dtype="f32", index="stretch",
+                 zround="symmetric", kernel="auto", tile_bins=0, order=0):
+        opt = hs_options(DTYPES[dtype], INDEX[index], ZROUND[zround], KERNELS[kernel],
+                         int(tile_bins), int(order))
+        self.n_templates, self.n_bins, self.H = n_templates, n_bins, H
+        self.dtype = dtype
+        self.handle = hs_plan_create(n_templates, n_bins, H, thresholds, opt)
+
+    @property
+    def kernel(self) -> str:
+        return {1: "generic", 2: "staged"}[lib().hs_plan_kernel(self.handle)]
+
+    @property
+    def tile_bins(self) -> int:
+        return lib().hs_plan_tile_bins(self.handle)
+
+    def run(self, fop, cands: CandBuffer, stream=None, fop_f32=None):
+        if fop_f32 is None:
+            hs_run(self.handle, fop, stream, cands.c)
+        else:
+            hs_run_checked(self.handle, fop, fop_f32, stream, cands.c)
+
+    def set_timing(self, enable=True):
+        hs_plan_set_timing(self.handle, enable)
+
+    def kernel_time(self):
+        """(summed kernel ms, launches) recorded since the last call."""
+        return hs_plan_kernel_time(self.handle)
+
+    def run_host(self, fop_host, fop_dev, cands: CandBuffer, host_records, stream=None):
+        return hs_run_host(self.handle, fop_host, fop_dev, cands.c, host_records, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            hs_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

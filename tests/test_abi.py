@@ -1,0 +1,92 @@
+"""CPU checks of the C ABI: the library builds, loads without a GPU, exports
+every function include/hs.h declares, and its host-side validation and
+helpers behave (no compute call needs a GPU here)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1805_12258_gb300 import build as hsbuild
+from paper_1805_12258_gb300 import hs
+
+
+@pytest.fixture(scope="module")
+def L():
+    hsbuild.build()
+    return hs.lib()
+
+
+def test_header_declares_the_boundary():
+    names = hs.header_functions()
+    for n in ("hs_plan_create", "hs_run", "hs_run_checked", "hs_cand_sync", "hs_run_host",
+              "hs_plan_destroy", "hs_status_str", "hs_last_error", "hs_pack_paper"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    missing = [n for n in hs.header_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_record_layout():
+    assert ctypes.sizeof(hs.hs_cand) == 16
+    assert hs.CAND_DTYPE.itemsize == 16
+    assert ctypes.sizeof(hs.hs_options) == 32
+
+
+def test_status_strings(L):
+    assert hs.hs_status_str(hs.HS_OK) == "ok"
+    assert "overflow" in hs.hs_status_str(hs.HS_ERR_OVERFLOW)
+    assert hs.hs_status_str(99) == "unknown status"
+
+
+@pytest.mark.parametrize("nt,n,H,why", [
+    (0, 100, 8, "odd"), (20, 100, 8, "odd"), (21, 0, 8, "n_bins"), (21, 100, 0, "H"),
+    (21, 100, 33, "H"), (32769, 100, 8, "odd"), (21, 1 << 31, 8, "n_bins")])
+def test_plan_create_rejects_bad_shapes(L, nt, n, H, why):
+    ta = np.ones(max(H, 1) * max(nt, 1), np.float32)
+    out = ctypes.c_void_p()
+    st = L.hs_plan_create(ctypes.byref(out), nt, n, H, ta.ctypes.data, None)
+    assert st == hs.HS_ERR_INVALID
+    assert why in L.hs_last_error().decode()
+    assert out.value is None
+
+
+def test_plan_create_rejects_nonfinite_thresholds(L):
+    ta = np.ones((8, 21), np.float32)
+    ta[3, 4] = np.nan
+    out = ctypes.c_void_p()
+    assert L.hs_plan_create(ctypes.byref(out), 21, 100, 8, ta.ctypes.data, None) == \
+        hs.HS_ERR_INVALID
+    assert L.hs_plan_create(ctypes.byref(out), 21, 100, 8, None, None) == hs.HS_ERR_INVALID
+
+
+def test_plan_create_rejects_bad_options(L):
+    ta = np.ones((8, 21), np.float32)
+    out = ctypes.c_void_p()
+    opt = hs.hs_options(7, 0, 0, 0, 0, 0)
+    assert L.hs_plan_create(ctypes.byref(out), 21, 100, 8, ta.ctypes.data,
+                            ctypes.byref(opt)) == hs.HS_ERR_INVALID
+
+
+def test_run_rejects_null_plan_and_pointers(L):
+    buf = hs.hs_cand_buf(None, None, 0)
+    assert L.hs_run(None, None, None, ctypes.byref(buf)) == hs.HS_ERR_INVALID
+    assert L.hs_cand_sync(None, None, None) == hs.HS_ERR_INVALID
+    assert L.hs_plan_destroy(None) == hs.HS_OK
+
+
+def test_pack_paper(L):
+    # Section III: CL1 = F*2^24 + H*2^21 + B with F the row, H the 0-based
+    # plane, B the bin; CL2 = amplitude.
+    rec = np.zeros(1, hs.CAND_DTYPE)[0]
+    rec["bin"], rec["z"], rec["k"], rec["power"] = 123456, -40, 8, 42.5
+    cl1, cl2 = hs.hs_pack_paper(rec, 85)
+    assert cl1 == (2 << 24) + (7 << 21) + 123456
+    assert cl2 == 42.5
+    rec["k"] = 9
+    with pytest.raises(hs.HsError):
+        hs.hs_pack_paper(rec, 85)
+    rec["k"], rec["bin"] = 1, 1 << 21
+    with pytest.raises(hs.HsError):
+        hs.hs_pack_paper(rec, 85)

@@ -1,0 +1,263 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerance: FP32 level sums within 1e-6 relative of the oracle (the FP32
+rounding bound of at most 15 ascending additions of non-negative terms is
+below 9e-7); candidate sets identical except for points the oracle lists
+within 1e-5 relative of their threshold.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1805_12258_gb300 import hs, synth
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-6
+NEAR = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_1805_12258_gb300 import build
+    build.build()
+    oracle.build()
+    torch.cuda.set_device(0)
+
+
+def run_gpu(plane, H, ta, *, cap=1 << 20, fop32=None, **plan_kw):
+    nt, n = plane.shape
+    if plane.dtype == np.uint16:  # bf16 bit patterns
+        fop = torch.from_numpy(plane.view(np.int16)).cuda().view(torch.bfloat16)
+    else:
+        fop = torch.from_numpy(np.ascontiguousarray(plane)).cuda()
+    cands = hs.CandBuffer(cap)
+    with hs.Plan(nt, n, H, ta, **plan_kw) as plan:
+        f32 = None if fop32 is None else torch.from_numpy(fop32).cuda()
+        plan.run(fop, cands, fop_f32=f32)
+        recs, count, st = cands.fetch()
+        kernel = plan.kernel
+    return recs, count, st, kernel
+
+
+def assert_matches_oracle(recs, ref, near, *, rtol=RTOL):
+    near_keys = {(int(c["k"]), int(c["z"]), int(c["f"])) for c in near}
+    g = {(int(r["k"]), int(r["z"]), int(r["bin"])): float(r["power"]) for r in recs}
+    o = {(int(c["k"]), int(c["z"]), int(c["f"])): float(c["power"]) for c in ref}
+    assert len(g) == len(recs), "duplicate candidate records"
+    only_gpu = set(g) - set(o) - near_keys
+    only_ora = set(o) - set(g) - near_keys
+    assert not only_gpu and not only_ora, (sorted(only_gpu)[:5], sorted(only_ora)[:5])
+    common = sorted(set(g) & set(o))
+    if common:
+        gv = np.array([g[k] for k in common])
+        ov = np.array([o[k] for k in common])
+        err = np.abs(gv - ov) / np.maximum(np.abs(ov), 1e-30)
+        assert err.max() <= rtol, (err.max(), common[int(err.argmax())])
+
+
+# --- the small plane (21 x 65,536, H = 8) -------------------------------------
+
+@pytest.mark.parametrize("kernel", ["staged", "generic"])
+def test_small_plane_candidates(kernel):
+    wl = synth.small_plane(seed=0)
+    plane = synth.make_plane(wl)
+    ta = synth.thresholds(wl.p_fa, wl.H, wl.n_templates)
+    recs, n, st, used = run_gpu(plane, wl.H, ta, kernel=kernel)
+    assert used == kernel and st == hs.HS_OK
+    ref, near = oracle.detect(plane, wl.H, ta, threads=8)
+    assert n == len(recs) and n > 0
+    assert_matches_oracle(recs, ref, near)
+
+
+# --- every level sum, by thresholds below every value --------------------------
+
+def _all_sums(plane, H, **kw):
+    nt, n = plane.shape
+    ta = np.full((H, nt), -1e30, np.float32)
+    recs, cnt, st, used = run_gpu(plane, H, ta, cap=nt * n * H, **kw)
+    assert st == hs.HS_OK and cnt == nt * n * H
+    Z = (nt - 1) // 2
+    got = np.empty((H, nt, n), np.float64)
+    got[recs["k"].astype(int) - 1, recs["z"].astype(int) + Z, recs["bin"].astype(int)] = \
+        recs["power"]
+    return got, used
+
+
+@pytest.mark.parametrize("nt,n,H,kernel", [
+    (21, 4096, 8, "staged"), (85, 2048, 16, "staged"), (21, 1000, 8, "staged"),
+    (85, 300, 16, "staged"), (21, 4096, 8, "generic"), (85, 1000, 16, "generic"),
+    (7, 333, 5, "generic"), (3, 5, 8, "generic"), (1, 17, 3, "generic"), (1, 1, 1, "generic"),
+    (33, 129, 32, "generic")])
+def test_every_level_sum(nt, n, H, kernel):
+    plane = synth.noise(nt, n, seed=nt * 1000 + n)
+    got, used = _all_sums(plane, H, kernel=kernel)
+    assert used == kernel
+    ref = oracle.planes(plane, H)
+    np.testing.assert_allclose(got, ref, rtol=RTOL, atol=0)
+
+
+@pytest.mark.parametrize("index,zround", [("hfrac", "symmetric"), ("stretch", "floor"),
+                                          ("hfrac", "floor")])
+def test_other_index_maps(index, zround):
+    plane = synth.noise(21, 777, seed=5)
+    got, used = _all_sums(plane, 8, index=index, zround=zround)
+    assert used == "generic"
+    ref = oracle.planes(plane, 8, index=oracle.HFRAC if index == "hfrac" else oracle.STRETCH,
+                        zround=oracle.ZFLOOR if zround == "floor" else oracle.ZSYM)
+    np.testing.assert_allclose(got, ref, rtol=RTOL, atol=0)
+
+
+def test_signed_inputs_take_the_exact_path():
+    # Negative inputs void the monotone-sum prefilter; the staged kernel must
+    # notice and test every level exactly.
+    plane = synth.random_plane(21, 4096, seed=3, lo=-1.0, hi=1.0)
+    plane[:, ::7] = np.abs(plane[:, ::7]) * 6.0
+    ta = np.tile(np.array([[0.9 + 0.3 * k] for k in range(8)], np.float32), (1, 21))
+    recs, n, st, used = run_gpu(plane, 8, ta)
+    assert used == "staged" and n > 0
+    ref, near = oracle.detect(plane, 8, ta)
+    # signed sums carry an absolute error bound: compare values with atol
+    assert_matches_oracle(recs, ref, near, rtol=1e-5)
+
+
+def test_per_row_thresholds():
+    plane = synth.noise(85, 4096, seed=21)
+    rng = np.random.default_rng(4)
+    ta = (synth.thresholds(1e-3, 16, 85) * rng.uniform(0.9, 1.3, size=(1, 85))).astype(np.float32)
+    recs, n, st, used = run_gpu(plane, 16, ta)
+    ref, near = oracle.detect(plane, 16, ta, threads=8)
+    assert used == "staged" and n > 100
+    assert_matches_oracle(recs, ref, near)
+
+
+# --- 16-bit storage --------------------------------------------------------------
+
+def _bf16_bits(x):
+    return torch.from_numpy(x).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+
+
+@pytest.mark.parametrize("nt,n,H", [(21, 8192, 8), (85, 4096, 16)])
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+def test_lowp_recheck_matches_fp32_path(nt, n, H, dtype):
+    plane = synth.noise(nt, n, seed=7)
+    ta = synth.thresholds(1e-3, H, nt)
+    r32, n32, _, _ = run_gpu(plane, H, ta)
+    low = _bf16_bits(plane) if dtype == "bf16" else plane.astype(np.float16)
+    rlp, nlp, st, used = run_gpu(low, H, ta, dtype=dtype, fop32=plane)
+    assert used == "staged" and st == hs.HS_OK
+    assert nlp == n32
+    assert np.array_equal(r32, rlp)  # same records, same FP32 powers
+    rg, ng, _, _ = run_gpu(low, H, ta, dtype=dtype, fop32=plane, kernel="generic")
+    assert np.array_equal(r32, rg)
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+def test_lowp_without_recheck_flags_band(dtype):
+    nt, n, H = 21, 8192, 8
+    plane = synth.noise(nt, n, seed=8)
+    ta = synth.thresholds(1e-3, H, nt)
+    low = _bf16_bits(plane) if dtype == "bf16" else plane.astype(np.float16)
+    recs, cnt, st, used = run_gpu(low, H, ta, dtype=dtype)
+    assert cnt > 0 and np.all(recs["flags"] & hs.HS_FLAG_LOWP)
+    # the oracle on the stored 16-bit values decides the same way except in the band
+    dc = oracle.DT_BF16 if dtype == "bf16" else None
+    ref, near = oracle.detect(low, H, ta, dtype_code=dc, near_rel=1e-5)
+    assert_matches_oracle(recs, ref, near, rtol=1e-6)
+    r32, _, _, _ = run_gpu(plane, H, ta)
+    k32 = {(int(r["k"]), int(r["z"]), int(r["bin"])) for r in r32}
+    klp = {(int(r["k"]), int(r["z"]), int(r["bin"])) for r in recs}
+    flagged = {(int(r["k"]), int(r["z"]), int(r["bin"])) for r in recs
+               if r["flags"] & hs.HS_FLAG_NEAR}
+    assert (klp - k32) <= flagged
+
+
+# --- buffers, ordering, end to end --------------------------------------------------
+
+def test_overflow_reports_true_count():
+    plane = synth.noise(21, 4096, seed=9)
+    ta = synth.thresholds(1e-2, 8, 21)
+    recs_all, n_all, _, _ = run_gpu(plane, 8, ta)
+    recs, n, st, _ = run_gpu(plane, 8, ta, cap=5)
+    assert st == hs.HS_ERR_OVERFLOW and n == n_all > 5 and len(recs) == 5
+
+
+def test_octave_order_same_result():
+    plane = synth.noise(85, 1 << 16, seed=10)
+    ta = synth.thresholds(1e-4, 16, 85)
+    a, na, _, _ = run_gpu(plane, 16, ta, order=1)
+    b, nb, _, _ = run_gpu(plane, 16, ta, order=2)
+    assert na == nb and np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("tb", [64, 256])
+def test_tile_widths_same_result(tb):
+    plane = synth.noise(85, 20000, seed=11)
+    ta = synth.thresholds(1e-4, 16, 85)
+    a, _, _, _ = run_gpu(plane, 16, ta)
+    b, _, _, used = run_gpu(plane, 16, ta, tile_bins=tb)
+    assert used == "staged" and np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("kernel", ["staged", "generic"])
+def test_run_host_matches_run(kernel):
+    wl = synth.small_plane(seed=2)
+    plane = synth.make_plane(wl)
+    ta = synth.thresholds(1e-4, wl.H, wl.n_templates)
+    ref, n_ref, _, _ = run_gpu(plane, wl.H, ta, kernel=kernel)
+    host = torch.from_numpy(plane).pin_memory()
+    dev = torch.empty_like(host, device="cuda")
+    cands = hs.CandBuffer(1 << 16)
+    out = np.zeros(1 << 16, hs.CAND_DTYPE)
+    with hs.Plan(wl.n_templates, wl.n_bins, wl.H, ta, kernel=kernel) as plan:
+        st, n = plan.run_host(host, dev, cands, out)
+    assert st == hs.HS_OK and n == n_ref
+    assert np.array_equal(hs.sort_records(out[:n]), ref)
+
+
+def test_launch_count_is_one():
+    plane = synth.noise(21, 4096, seed=12)
+    run_gpu(plane, 8, synth.thresholds(1e-3, 8, 21))
+    # the last hs_run on this thread launched exactly one kernel
+    assert hs.hs_last_launch_count() == 1
+
+
+# --- the SKA plane at full size (85 x 2^21, H = 16), bench launch configuration ----
+
+@pytest.fixture(scope="module")
+def ska():
+    wl = synth.ska_plane(seed=1)
+    plane = synth.make_plane(wl)
+    ta = synth.thresholds(wl.p_fa, wl.H, wl.n_templates)
+    return wl, plane, ta
+
+
+def test_ska_plane_candidates(ska):
+    wl, plane, ta = ska
+    recs, n, st, used = run_gpu(plane, wl.H, ta)
+    assert used == "staged" and st == hs.HS_OK
+    ref, near = oracle.detect(plane, wl.H, ta, threads=16)
+    assert_matches_oracle(recs, ref, near)
+
+
+@pytest.mark.parametrize("z", [0, -42, 17])
+def test_ska_plane_row_sums(ska, z):
+    # Every level sum of one full row (2^21 bins x 16 levels), checked
+    # against the oracle point by point: the row's thresholds are set below
+    # every value so each sum becomes a record.
+    wl, plane, ta = ska
+    Z = (wl.n_templates - 1) // 2
+    ta2 = ta.copy()
+    ta2[:, z + Z] = -1e30
+    recs, n, st, _ = run_gpu(plane, wl.H, ta2, cap=wl.n_bins * wl.H + (1 << 16))
+    assert st == hs.HS_OK
+    row = recs[recs["z"] == z]
+    assert len(row) == wl.n_bins * wl.H
+    got = np.empty((wl.n_bins, wl.H))
+    got[row["bin"].astype(np.int64), row["k"].astype(np.int64) - 1] = row["power"]
+    f = np.arange(wl.n_bins, dtype=np.int64)
+    ref = oracle.sample(plane, wl.H, np.full(wl.n_bins, z, np.int32), f)
+    np.testing.assert_allclose(got, ref, rtol=RTOL, atol=0)
