@@ -173,6 +173,7 @@ hs_status launch_range(hs_plan *p, const void *fop, const float *fop32, cudaStre
         L.sh = StagedShape{p->nt, p->H, p->tb, p->opt.dtype};
         L.maps = p->maps;
         L.tmin_host = p->tmin.data();
+        L.fop = fop;
         L.ta = p->d_ta;
         L.fop32 = fop32;
         L.order = full ? p->d_order : nullptr;
@@ -322,12 +323,15 @@ hs_status hs_plan_create(hs_plan **out, int n_templates, int64_t n_bins, int H,
             for (int k = a; k <= ends[g]; ++k)
                 for (int r = 0; r < n_templates; ++r)
                     t = std::min(t, (double)p->ta[(size_t)(k - 1) * n_templates + r]);
-            // exact condition s (1 + delta) > t - band_abs, rounded down
+            // A hit needs s (1 + delta) > t - band_abs; the fast pass sums a
+            // group in tree order, within 2*gamma_H of the ascending sum, so
+            // the bound is lowered by a further relative H*2^-22 (> 2 gamma_H)
             double lowered = (t - p->band_abs) / (1.0 + p->delta);
+            lowered -= std::fabs(lowered) * H * std::ldexp(1.0, -22);
             float lf = (float)lowered;
             if ((double)lf > lowered)
                 lf = std::nextafter(lf, -INFINITY);
-            p->tmin[g] = p->delta == 0.f ? (float)t : lf;
+            p->tmin[g] = lf;
             a = ends[g] + 1;
         }
         p->n_tiles = (int)((n_bins + p->tb - 1) / p->tb);

@@ -51,9 +51,10 @@ int staged_groups(int H, int *ends);
 
 struct StagedLaunch {
     StagedShape sh;
-    const CUtensorMap *maps;  // host copies, H entries (encoded for this plane)
+    const CUtensorMap *maps;  // host copies, H descriptors (encoded for this plane)
     const float *tmin_host;   // prefilter thresholds [groups] (min over rows)
     const float *ta;          // device thresholds [H][nt]
+    const void *fop;          // the plane (device)
     const float *fop32;       // recheck copy or null
     const uint32_t *order;    // device tile order (null = linear)
     float delta;

@@ -1,39 +1,35 @@
 // hs_staged.cu -- the staged harmonic-summing kernel (the hot path).
 //
-// One CTA owns an output tile of TB consecutive bins [f0, f0+TB) x all NT
-// template rows.  For each stretch factor m = 1..H (Eq. 1) the tile reads the
-// input span rows [Z - Z/m, Z + Z/m] x bins [floor(f0/m), floor((f0+TB-1)/m)];
-// one elected thread stages every span into shared memory with one 2-D TMA
-// box per m, all completing on a single mbarrier, so each plane point crosses
-// HBM about once per tile that needs it (the "load the necessary points of a
-// chunk" idea of Section IV-C2, with TMA boxes instead of the paper's
-// reordered plane).
+// Work unit: a tile of TB consecutive bins [f0, f0+TB) x all NT template
+// rows, one CTA of TB threads; thread t owns bin f = f0 + t and every row.
+// For each stretch factor m = 1..H (Eq. 1) the tile reads the input span
+// rows [Z - Z/m, Z + Z/m] x bins [floor(f0/m), floor((f0+TB-1)/m)] -- the
+// "necessary points" of the chunk (Section IV-C2), gathered with 2-D TMA
+// boxes instead of the paper's reordered plane -- so each plane point crosses
+// HBM about once per tile that needs it.  One elected thread issues one box
+// per m, all completing on a single mbarrier.
 //
-// Each thread then owns one bin f and all NT rows of the tile.  Rows are
-// walked outward from z = 0 as mirrored pairs (+zz, -zz): under the
-// symmetric rounding rho(z, m) = sign(z) floor(|z|/m) the two rows of a pair
+// Rows are walked outward from z = 0 as mirrored pairs (+zz, -zz).  Under the
+// symmetric rounding rho(z, m) = sign(z) floor(|z|/m) both rows of a pair
 // change their source row for the same m, so the values of all m stay in
-// registers and are reloaded from shared memory only when m divides zz.  The
-// pair's H cumulative sums of Eq. 2 are formed with packed FP32 adds
-// (add.rn.f32x2), in ascending m -- the order of Eq. 2, so every sum is the
-// same FP32 number as a plain scalar loop.
+// registers and are reloaded from shared memory only when m divides zz.
 //
-// Detection uses an exact two-stage test.  With non-negative inputs a level
-// sum never decreases with k, so "no level in [a, b] exceeds its threshold"
-// follows from HP_b <= min_{k in [a,b]} TA(k, row), and a fortiori from
-// HP_b <= the smallest threshold of the group over all rows, which is the
-// bound used (four values held in registers; per-row bounds would have to
-// be re-read for every row and cost more than they save).  The fast pass tests only
-// the level groups [1,2], [3,4], [5,8], [9,16] this way and marks the row pairs
-// that might hold a hit; a slow pass recomputes those pairs level by level and
-// appends the true hits (warp ballot + prefix, one atomic per warp).  A thread
-// that loaded any value with its sign bit set (negative input, -0) sends all
-// of its rows to the slow pass, so the result never depends on the inputs
-// being non-negative.  For 16-bit planes the group thresholds are lowered by
-// the storage error bound and the slow pass re-evaluates possible hits from
-// the FP32 copy, so candidates match the FP32 path.
+// Detection is exact in two stages.  With non-negative inputs a level sum
+// never decreases with k, so "no level in [a, b] exceeds its threshold"
+// follows from HP_b <= min over the group's levels and all rows of TA, the
+// group bound (a few values in registers; per-row bounds would have to be
+// re-read for every row and cost more than they save).  The fast pass forms
+// HP_b only at the group ends (each group summed as a tree with packed FP32
+// adds over the pair, the bound lowered by that order's FP32 error) and marks
+// the row pairs that might hold a hit; the slow pass recomputes those rows
+// level by level in ascending m (the order of Eq. 2) and appends the true
+// hits with warp ballot + prefix and one atomic per warp.  A thread that
+// loaded any value with its sign bit set (a negative input or -0) sends all
+// its rows to the slow pass, so the result never depends on the inputs being
+// non-negative.  For 16-bit planes the bounds are lowered by the storage
+// error too and the slow pass re-evaluates possible hits from the FP32 copy,
+// so candidates match the FP32 path record for record.
 #include <cstring>
-#include <mutex>
 
 #include "hs_device.cuh"
 #include "hs_internal.h"
@@ -42,10 +38,14 @@ namespace hs {
 namespace {
 
 constexpr int round_up(int x, int a) { return (x + a - 1) / a * a; }
+constexpr int cmin(int a, int b) { return a < b ? a : b; }
 
-// Level groups of the prefilter: a group ends at every power of two >= 2
-// and at H.
-constexpr bool group_end(int m, int H) { return m == H || (m >= 2 && (m & (m - 1)) == 0); }
+// Level groups of the prefilter: a group ends at 2, 4, 8, then every 4
+// levels, and at H.
+constexpr bool group_end(int m, int H)
+{
+    return m == H || m == 2 || m == 4 || (m >= 8 && m % 4 == 0);
+}
 constexpr int group_index(int m, int H)
 {
     int g = 0;
@@ -61,6 +61,15 @@ struct Cfg {
     static constexpr int ES = (int)sizeof(T);
     static constexpr int ALIGN = 16 / ES; // elements per 16 bytes (TMA x alignment)
     static constexpr int G = n_groups(H);
+    // first and last level of prefilter group g
+    static constexpr int GHI(int g)
+    {
+        for (int m = 1, i = 0; m <= H; ++m)
+            if (group_end(m, H) && i++ == g)
+                return m;
+        return H;
+    }
+    static constexpr int GLO(int g) { return g == 0 ? 1 : GHI(g - 1) + 1; }
     static constexpr int R(int m) { return Z / m; }
     static constexpr int ROWS(int m) { return 2 * R(m) + 1; }
     // Box width: exact when every tile start f0/m is 16-byte aligned,
@@ -87,15 +96,15 @@ struct Cfg {
     }
     static_assert(NT % 2 == 1, "odd template count");
     static_assert(Z <= 63, "row-pair mask is 64 bits");
-    static_assert(H <= kMaxStagedH && G <= kMaxGroups, "level count");
-    static_assert(TB <= 256 && TB % ALIGN == 0, "TMA box width");
+    static_assert(H >= 2 && H <= kMaxStagedH && G <= kMaxGroups, "level count");
+    static_assert(TB <= 256 && TB % ALIGN == 0 && TB % 32 == 0, "TMA box width, whole warps");
     static_assert(TX() < (1 << 20), "mbarrier transaction count");
 };
 
-template <int NT, int H>
+template <int NT, int H, typename T>
 struct Params {
-    CUtensorMap maps[H];    // one 2-D box per stretch factor m
-    float tmin[n_groups(H)]; // prefilter threshold per level group (min over rows)
+    CUtensorMap maps[H];    // one 2-D box per stretch factor m (its whole span)
+    float tmin[n_groups(H)]; // prefilter bound per level group (min over rows)
     const float *ta;        // exact thresholds [H][NT] (device)
     const float *fop32;     // FP32 copy for rechecks, or null
     const uint32_t *order;  // tile order (device) or null
@@ -105,8 +114,20 @@ struct Params {
     float delta;            // 16-bit storage relative error bound (0 for FP32)
     float band_abs;         // 16-bit storage absolute error bound
     long long n;
-    int tile_lo;
+    int tile_lo;            // first slot of the tile order this launch covers
 };
+
+// Pairwise (tree) sum of cur[LO..HI] with packed adds; depth log2(HI-LO+1).
+template <int LO, int HI, int N>
+__device__ __forceinline__ float2 tree_sum(const float2 (&cur)[N])
+{
+    if constexpr (LO == HI) {
+        return cur[LO];
+    } else {
+        constexpr int MID = (LO + HI) / 2;
+        return __fadd2_rn(tree_sum<LO, MID>(cur), tree_sum<MID + 1, HI>(cur));
+    }
+}
 
 // Level m value of the FP32 copy at (z, f): the Eq. 2 chain in FP32,
 // ascending m, i.e. exactly the number the FP32 path computes.
@@ -121,20 +142,26 @@ __device__ float chain_f32(const float *fop32, int Z, long long n, int z, int f,
     return s;
 }
 
+// CTAs per SM the register budget is sized for
+#ifndef HS_STAGED_MINB
+#define HS_STAGED_MINB 3
+#endif
+
 template <int NT, int H, int TB, typename T>
-__global__ void __launch_bounds__(TB, 384 / TB) staged_kernel(const __grid_constant__ Params<NT, H> p)
+__global__ void __launch_bounds__(TB, HS_STAGED_MINB * 128 / TB)
+    staged_kernel(const __grid_constant__ Params<NT, H, T> p)
 {
     using C = Cfg<NT, H, TB, T>;
     constexpr int Z = C::Z;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar_storage;
 
-    const uint32_t bar = smem_addr(&bar_storage);
-    const uint32_t sbase = smem_addr(smem);
     const int tid = threadIdx.x;
     const int slot = p.tile_lo + (int)blockIdx.x;
     const int tile = p.order ? (int)__ldg(p.order + slot) : slot;
     const int f0 = tile * TB;
+    const uint32_t sbase = smem_addr(smem);
+    const uint32_t bar = smem_addr(&bar_storage);
 
     if (tid == 0) {
         static_for<0, H>([&](auto M) { prefetch_tmap(&p.maps[M]); });
@@ -164,58 +191,63 @@ __global__ void __launch_bounds__(TB, 384 / TB) staged_kernel(const __grid_const
 
     bool ok = mbar_wait_bounded(bar, 0, kWaitLimitNs);
     ok = __all_sync(0xffffffffu, ok);
+
+    // ---- fast pass: every row pair, group prefilter ------------------------------
+    // d = HP_b - bound has its sign bit set exactly when HP_b < bound (IEEE
+    // subtraction is sign-exact without flush-to-zero), so AND-ing the sign
+    // bits of every group's d leaves bit 31 set iff no group of the pair can
+    // hold a hit.
+    float2 ntg[C::G];
+    static_for<0, C::G>([&](auto g) { ntg[g] = make_float2(-p.tmin[g], -p.tmin[g]); });
+    uint32_t negbits = 0u;
+    uint64_t mask = 0ull;
+    float2 cur[H];
+    auto pair_test = [&]() -> uint32_t {
+        float2 acc = make_float2(0.f, 0.f);
+        uint32_t sgn = 0xffffffffu;
+        static_for<0, C::G>([&](auto g) {
+            constexpr int lo = C::GLO(g), hi = C::GHI(g);
+            const float2 gs = tree_sum<lo - 1, hi - 1>(cur);
+            if constexpr (g == 0)
+                acc = gs;
+            else
+                acc = __fadd2_rn(acc, gs);
+            const float2 d = __fadd2_rn(acc, ntg[g]);
+            sgn &= __float_as_uint(d.x) & __float_as_uint(d.y);
+        });
+        return (~sgn) >> 31; // 1: the pair may hold a hit
+    };
+    if (ok) {
+        // template z = 0: every stretch reads the centre row
+        static_for<0, H>([&](auto M) {
+            const float v = to_f32(sm[bidx[M]]);
+            cur[M] = make_float2(v, v);
+            negbits |= __float_as_uint(v);
+        });
+        mask = pair_test();
+        // pairs (+zz, -zz): reload the value of m only when m divides zz
+        static_for<1, Z + 1>([&](auto ZZ) {
+            constexpr int zz = ZZ;
+            static_for<0, H>([&](auto M) {
+                constexpr int m = M + 1;
+                if constexpr (zz % m == 0) {
+                    constexpr int off = (zz / m) * C::W(m);
+                    const float tv = to_f32(sm[bidx[M] + off]);
+                    const float bv = to_f32(sm[bidx[M] - off]);
+                    cur[M] = make_float2(tv, bv);
+                    negbits |= __float_as_uint(tv) | __float_as_uint(bv);
+                }
+            });
+            mask |= (uint64_t)pair_test() << zz;
+        });
+    }
     if (!ok) {
         if ((tid & 31) == 0)
             set_status(p.counters, HS_ERR_TIMEOUT);
         mbar_wait_bounded(bar, 0, kWaitLimitNs); // let copies in flight land
+
         return;
     }
-
-    // ---- fast pass: all rows, group prefilter --------------------------------
-    float tg[C::G];
-    static_for<0, C::G>([&](auto g) { tg[g] = p.tmin[g]; });
-    uint32_t negbits = 0u;
-    uint64_t mask = 0ull;
-    float2 cur[H];
-    {
-        float acc = 0.f;
-        bool maybe = false;
-        static_for<0, H>([&](auto M) {
-            constexpr int m = M + 1;
-            const float v = to_f32(sm[bidx[M]]);
-            cur[M] = make_float2(v, v);
-            negbits |= __float_as_uint(v);
-            acc = (m == 1) ? v : acc + v;
-            if constexpr (group_end(m, H))
-                maybe |= !(acc <= tg[group_index(m, H)]);
-        });
-        mask = maybe ? 1ull : 0ull;
-    }
-    static_for<1, Z + 1>([&](auto ZZ) {
-        constexpr int zz = ZZ;
-        float2 acc = cur[0];
-        bool maybe = false;
-        static_for<0, H>([&](auto M) {
-            constexpr int m = M + 1;
-            if constexpr (zz % m == 0) {
-                constexpr int off = (zz / m) * C::W(m);
-                const float t = to_f32(sm[bidx[M] + off]);
-                const float b = to_f32(sm[bidx[M] - off]);
-                cur[M] = make_float2(t, b);
-                negbits |= __float_as_uint(t) | __float_as_uint(b);
-            }
-            if constexpr (m == 1)
-                acc = cur[0];
-            else
-                acc = __fadd2_rn(acc, cur[M]);
-            if constexpr (group_end(m, H)) {
-                maybe |= !(acc.x <= tg[group_index(m, H)]);
-                maybe |= !(acc.y <= tg[group_index(m, H)]);
-            }
-        });
-        if (maybe)
-            mask |= 1ull << zz;
-    });
     if (!valid)
         mask = 0ull;
     else if (negbits >> 31)
@@ -227,28 +259,29 @@ __global__ void __launch_bounds__(TB, 384 / TB) staged_kernel(const __grid_const
     auto scan = [&](int z, bool write, uint32_t rslot) -> uint32_t {
         float acc = 0.f, ab = 0.f;
         uint32_t hits = 0u;
+        float thr[H];
+        static_for<0, H>([&](auto M) { thr[M] = __ldg(p.ta + M * NT + (z + Z)); });
         static_for<0, H>([&](auto M) {
             constexpr int m = M + 1;
             const int rho = z >= 0 ? z / m : -((-z) / m);
             const float v = to_f32(sm[bidx[M] + rho * C::W(m)]);
             acc = (m == 1) ? v : acc + v;
             ab += fabsf(v);
-            const float thr = __ldg(p.ta + M * NT + (z + Z));
             float power = acc;
             uint32_t flags = 0u;
             bool hit;
             if (p.delta == 0.f) {
-                hit = acc > thr;
+                hit = acc > thr[M];
             } else if (p.fop32 != nullptr) {
                 hit = false;
-                if (!(acc == acc && acc + (p.delta * ab + p.band_abs) < thr)) {
+                if (!(acc == acc && acc + (p.delta * ab + p.band_abs) < thr[M])) {
                     power = chain_f32(p.fop32, Z, p.n, z, f, m);
-                    hit = power > thr;
+                    hit = power > thr[M];
                 }
             } else {
-                hit = acc > thr;
+                hit = acc > thr[M];
                 flags = HS_FLAG_LOWP |
-                        (fabsf(acc - thr) <= p.delta * ab + p.band_abs ? HS_FLAG_NEAR : 0u);
+                        (fabsf(acc - thr[M]) <= p.delta * ab + p.band_abs ? HS_FLAG_NEAR : 0u);
             }
             if (hit) {
                 hits |= 1u << M;
@@ -271,11 +304,11 @@ __global__ void __launch_bounds__(TB, 384 / TB) staged_kernel(const __grid_const
             if (zz > 0)
                 hb = scan(-zz, false, 0u);
         }
-        uint32_t rs = warp_reserve(p.counters, (uint32_t)(__popc(ht) + __popc(hb)));
+        uint32_t rsl = warp_reserve(p.counters, (uint32_t)(__popc(ht) + __popc(hb)));
         if (ht)
-            scan(zz, true, rs);
+            scan(zz, true, rsl);
         if (hb)
-            scan(-zz, true, rs + (uint32_t)__popc(ht));
+            scan(-zz, true, rsl + (uint32_t)__popc(ht));
     }
 }
 
@@ -283,7 +316,7 @@ template <int NT, int H, int TB, typename T>
 cudaError_t launch_one(const StagedLaunch &a, cudaStream_t s)
 {
     using C = Cfg<NT, H, TB, T>;
-    Params<NT, H> p;
+    Params<NT, H, T> p;
     std::memset(&p, 0, sizeof p);
     std::memcpy(p.maps, a.maps, sizeof(CUtensorMap) * H);
     for (int g = 0; g < C::G; ++g)
@@ -298,30 +331,16 @@ cudaError_t launch_one(const StagedLaunch &a, cudaStream_t s)
     p.band_abs = a.band_abs;
     p.n = a.n;
     p.tile_lo = a.tile_lo;
-    auto kern = staged_kernel<NT, H, TB, T>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         C::SMEM);
-    if (e != cudaSuccess)
-        return e;
     const int tiles = a.tile_hi - a.tile_lo;
     if (tiles <= 0)
         return cudaSuccess;
+    auto kern = staged_kernel<NT, H, TB, T>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess)
+        return e;
     kern<<<tiles, TB, C::SMEM, s>>>(p);
     return cudaGetLastError();
 }
-
-// Shapes compiled into the library: the SKA plane (85 templates, 16 levels),
-// the small plane (21 templates, 8 levels), each for FP32, BF16 and FP16
-// storage; tile widths 64/128/256 for the FP32 SKA shape (autotuner choices).
-#define HS_STAGED_SHAPES(X)                                                                   \
-    X(85, 16, 128, float, HS_F32)                                                             \
-    X(85, 16, 64, float, HS_F32)                                                              \
-    X(85, 16, 256, float, HS_F32)                                                             \
-    X(85, 16, 128, __nv_bfloat16, HS_BF16)                                                    \
-    X(85, 16, 128, __half, HS_F16)                                                            \
-    X(21, 8, 128, float, HS_F32)                                                              \
-    X(21, 8, 128, __nv_bfloat16, HS_BF16)                                                     \
-    X(21, 8, 128, __half, HS_F16)
 
 template <int NT, int H, int TB, typename T>
 void box_of(int m, int *w, int *rows)
@@ -330,12 +349,25 @@ void box_of(int m, int *w, int *rows)
     *rows = Cfg<NT, H, TB, T>::ROWS(m);
 }
 
+// Shapes compiled into the library: the SKA plane (85 templates, 16 levels),
+// the small plane (21 templates, 8 levels), each for FP32, BF16 and FP16
+// storage; tile widths 64/96/128 for the FP32 SKA shape (autotuner choices).
+#define HS_STAGED_SHAPES(X)                                                                   \
+    X(85, 16, 128, float, HS_F32)                                                             \
+    X(85, 16, 64, float, HS_F32)                                                              \
+    X(85, 16, 96, float, HS_F32)                                                              \
+    X(85, 16, 128, __nv_bfloat16, HS_BF16)                                                    \
+    X(85, 16, 128, __half, HS_F16)                                                            \
+    X(21, 8, 128, float, HS_F32)                                                              \
+    X(21, 8, 128, __nv_bfloat16, HS_BF16)                                                     \
+    X(21, 8, 128, __half, HS_F16)
+
 } // namespace
 
 bool staged_available(const StagedShape &sh)
 {
-#define X(NT_, H_, TB_, T_, DT_)                                                                   \
-    if (sh.nt == NT_ && sh.H == H_ && sh.tb == TB_ && sh.dtype == DT_)                           \
+#define X(NT_, H_, TB_, T_, DT_)                                                              \
+    if (sh.nt == NT_ && sh.H == H_ && sh.tb == TB_ && sh.dtype == DT_)                       \
         return true;
     HS_STAGED_SHAPES(X)
 #undef X
@@ -344,8 +376,8 @@ bool staged_available(const StagedShape &sh)
 
 int staged_smem_bytes(const StagedShape &sh)
 {
-#define X(NT_, H_, TB_, T_, DT_)                                                                   \
-    if (sh.nt == NT_ && sh.H == H_ && sh.tb == TB_ && sh.dtype == DT_)                           \
+#define X(NT_, H_, TB_, T_, DT_)                                                              \
+    if (sh.nt == NT_ && sh.H == H_ && sh.tb == TB_ && sh.dtype == DT_)                       \
         return Cfg<NT_, H_, TB_, T_>::SMEM;
     HS_STAGED_SHAPES(X)
 #undef X
@@ -355,9 +387,9 @@ int staged_smem_bytes(const StagedShape &sh)
 void staged_box(const StagedShape &sh, int m, int *width, int *rows)
 {
     *width = *rows = 0;
-#define X(NT_, H_, TB_, T_, DT_)                                                                   \
-    if (sh.nt == NT_ && sh.H == H_ && sh.tb == TB_ && sh.dtype == DT_) {                         \
-        box_of<NT_, H_, TB_, T_>(m, width, rows);                                                 \
+#define X(NT_, H_, TB_, T_, DT_)                                                              \
+    if (sh.nt == NT_ && sh.H == H_ && sh.tb == TB_ && sh.dtype == DT_) {                     \
+        box_of<NT_, H_, TB_, T_>(m, width, rows);                                             \
         return;                                                                               \
     }
     HS_STAGED_SHAPES(X)
@@ -376,8 +408,8 @@ int staged_groups(int H, int *ends)
 cudaError_t launch_staged(const StagedLaunch &a, cudaStream_t s)
 {
     const StagedShape &sh = a.sh;
-#define X(NT_, H_, TB_, T_, DT_)                                                                   \
-    if (sh.nt == NT_ && sh.H == H_ && sh.tb == TB_ && sh.dtype == DT_)                           \
+#define X(NT_, H_, TB_, T_, DT_)                                                              \
+    if (sh.nt == NT_ && sh.H == H_ && sh.tb == TB_ && sh.dtype == DT_)                       \
         return launch_one<NT_, H_, TB_, T_>(a, s);
     HS_STAGED_SHAPES(X)
 #undef X

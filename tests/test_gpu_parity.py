@@ -193,7 +193,18 @@ def test_octave_order_same_result():
     assert na == nb and np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("tb", [64, 256])
+def test_long_tile_walk_matches_generic():
+    # Many tiles per CTA: every stage of the persistent ring is refilled many
+    # times.  The staged and generic kernels must return identical records.
+    plane = synth.noise(21, 1 << 20, seed=13)
+    ta = synth.thresholds(1e-4, 8, 21)
+    a, na, sa, ua = run_gpu(plane, 8, ta)
+    b, nb, sb, ub = run_gpu(plane, 8, ta, kernel="generic")
+    assert ua == "staged" and ub == "generic" and sa == sb == hs.HS_OK
+    assert na == nb > 0 and np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("tb", [64, 96])
 def test_tile_widths_same_result(tb):
     plane = synth.noise(85, 20000, seed=11)
     ta = synth.thresholds(1e-4, 16, 85)
