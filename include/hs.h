@@ -72,7 +72,7 @@ typedef struct {
     int zround;     /* hs_zround (default HS_ZROUND_SYMMETRIC) */
     int kernel;     /* hs_kernel: AUTO picks the staged kernel when it applies */
     int tile_bins;  /* bins per CTA of the staged kernel: 0 = default */
-    int order;      /* tile order: 0 = default, 1 = linear, 2 = octave-interleaved */
+    int order;      /* tile order: 0 = default (octave), 1 = linear, 2 = octave-interleaved */
     int reserved[2];
 } hs_options;
 

@@ -335,7 +335,7 @@ hs_status hs_plan_create(hs_plan **out, int n_templates, int64_t n_bins, int H,
             a = ends[g] + 1;
         }
         p->n_tiles = (int)((n_bins + p->tb - 1) / p->tb);
-        const int kind = o.order == 0 ? 1 : o.order;
+        const int kind = o.order == 0 ? 2 : o.order; // default: octave-interleaved
         std::vector<uint32_t> ord = tile_order(p->n_tiles, kind);
         e = cudaMalloc(&p->d_order, sizeof(uint32_t) * ord.size());
         if (e == cudaSuccess)

@@ -336,6 +336,8 @@ cudaError_t launch_one(const StagedLaunch &a, cudaStream_t s)
         return cudaSuccess;
     auto kern = staged_kernel<NT, H, TB, T>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e == cudaSuccess) // all of the unified L1/shared storage as shared memory
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess)
         return e;
     kern<<<tiles, TB, C::SMEM, s>>>(p);
