@@ -155,6 +155,29 @@ HS_API hs_status hs_run_host(hs_plan *plan, const void *fop_host, void *fop_dev,
                       const hs_cand_buf *cands, hs_cand *host_records,
                       uint32_t host_capacity, hs_stream_t stream, uint32_t *n_out);
 
+/* Harmonic summing with no device allocation.  The paper has no counterpart:
+ * this entry point is for callers that may not allocate device memory, such
+ * as code inside a host framework that has reserved all device memory for its
+ * own pool, or latency-critical loops that cannot afford cudaMalloc/cudaFree
+ * (they may synchronise the device).  It does what hs_plan_create + hs_run +
+ * hs_plan_destroy do for an FP32 plane with the default options, without a
+ * plan and without allocating: the threshold table is copied into a fixed
+ * array inside the library's device image, and tiles run in linear order.
+ *  - Limit: H * n_templates <= 16384 (a 64 KiB table); larger requests fail
+ *    with HS_ERR_INVALID.  Every GPU that loads the library holds the array
+ *    until the process exits.
+ *  - The first call on a device looks up the array's device address with
+ *    that device current (cudaGetSymbolAddress); make that first call before
+ *    any stream capture.
+ *  - All calls share the array and it keeps the last call's thresholds: two
+ *    calls whose work overlaps on the GPU (different streams, or threads)
+ *    race on it.  Serialise them, e.g. issue them on one stream.
+ *  - fop, stream and cands as for hs_run (the counters are reset on stream).
+ * Errors: HS_ERR_INVALID, HS_ERR_CUDA; device timeouts via hs_cand_sync. */
+HS_API hs_status hs_run_noalloc(int n_templates, int64_t n_bins, int H, const float *thresholds,
+                                const void *fop, hs_stream_t stream, const hs_cand_buf *cands);
+HS_API const char *hs_noalloc_last_error(void);
+
 /* Destroy a plan (NULL is accepted).  Synchronises the device first. */
 HS_API hs_status hs_plan_destroy(hs_plan *plan);
 

@@ -93,6 +93,10 @@ def lib():
     L.hs_plan_set_timing.argtypes = [vp, i32]
     L.hs_plan_kernel_time.argtypes = [vp, P(ctypes.c_double), P(i32)]
     L.hs_pack_paper.argtypes = [P(hs_cand), i32, P(u32), P(ctypes.c_float)]
+    L.hs_run_noalloc.argtypes = [i32, i64, i32, vp, vp, vp, P(hs_cand_buf)]
+    L.hs_run_noalloc.restype = i32
+    L.hs_noalloc_last_error.argtypes = []
+    L.hs_noalloc_last_error.restype = ctypes.c_char_p
     L.hs_status_str.argtypes = [i32]
     L.hs_status_str.restype = ctypes.c_char_p
     L.hs_last_error.argtypes = []
@@ -173,6 +177,21 @@ def hs_run_host(plan, fop_host, fop_dev, cands: hs_cand_buf, host_records, strea
                            ctypes.byref(n))
     _check(st, "hs_run_host", ok=(HS_OK, HS_ERR_OVERFLOW))
     return st, n.value
+
+
+def hs_run_noalloc(n_templates, n_bins, H, thresholds, fop, stream, cands: hs_cand_buf):
+    """hs_run without a plan and without device allocation (see include/hs.h):
+    for callers that may not allocate device memory.  H * n_templates must be
+    at most 16384; calls share one static threshold table, so calls that
+    overlap on the GPU race."""
+    ta = np.ascontiguousarray(thresholds, dtype=np.float32)
+    if ta.shape != (H, n_templates):
+        raise ValueError(f"thresholds must have shape {(H, n_templates)}, got {ta.shape}")
+    st = lib().hs_run_noalloc(n_templates, n_bins, H, ta.ctypes.data, _ptr(fop),
+                              _stream_handle(stream), ctypes.byref(cands))
+    if st != HS_OK:
+        raise HsError(st, f"hs_run_noalloc: {lib().hs_noalloc_last_error().decode()}")
+    return st
 
 
 def hs_plan_destroy(plan):
