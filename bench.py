@@ -43,8 +43,8 @@ L2_BYTES = 129 * 2**20
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ska", choices=["ska", "small"])
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"])
@@ -133,20 +133,22 @@ def oracle_sample(plane, ta, H, cpu_seconds, threads):
     import oracle
     oracle.build()
     nt, n = plane.shape
-    mid = n // 2
     # calibrate: per-point cost on a small window, one thread
     cal = 2048
     t0 = time.perf_counter()
-    oracle.detect(plane, H, ta, f_lo=mid, f_hi=mid + cal, threads=1)
+    oracle.detect(plane, H, ta, f_lo=n // 2, f_hi=n // 2 + cal, threads=1)
     per_point = (time.perf_counter() - t0) / (nt * cal)
+    # bins [n - bins, n): the high bins, whose stretch reads span the plane
     bins = int(cpu_seconds / max(per_point, 1e-12) / nt)
-    bins = max(threads * 64, min(bins, n - mid))
+    bins = max(min(n, threads * 64), min(bins, n))
+    lo = n - bins
     t0 = time.perf_counter()
-    cands, _ = oracle.detect(plane, H, ta, f_lo=mid, f_hi=mid + bins, threads=threads)
+    cands, _ = oracle.detect(plane, H, ta, f_lo=lo, f_hi=n, threads=threads)
     dt = time.perf_counter() - t0
+    what = "the whole plane" if bins == n else f"bins [{lo}, {n}) of the same plane"
     return {"value": nt * bins / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"all {nt} rows x bins [{mid}, {mid + bins}) of the same plane "
-                      f"({nt * bins} points, {H} levels, FP64), {threads} threads",
+            "sample": f"all {nt} rows x {what} ({nt * bins} points, {H} levels, FP64), "
+                      f"{threads} threads",
             "seconds": dt, "candidates_in_sample": int(len(cands))}
 
 
@@ -168,16 +170,18 @@ def kernel_source_hash():
 def profiled_traffic(name):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
         with open(path) as fh:
-            d = json.load(fh)
-    except (OSError, ValueError):
+            lines = [ln.split("|") for ln in fh if ln.strip() and not ln.startswith("#")]
+    except OSError:
         return None
-    e = d.get(name)
-    if not e or e.get("kernel_sha") != kernel_source_hash():
-        return None
-    return e.get("dram_bytes_per_launch")
+    sha = kernel_source_hash()
+    for parts in lines:
+        parts = [x.strip() for x in parts]
+        if len(parts) >= 3 and parts[0] == name and parts[2] == sha:
+            return int(parts[1])
+    return None
 
 
 def peaks():
