@@ -46,7 +46,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ska", choices=["ska", "small"])
+    ap.add_argument("--workload", default="ska", choices=["ska", "small", "batch"])
+    ap.add_argument("--grid-per-sm", type=int, default=0)
+    ap.add_argument("--beams", type=int, default=64)
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--order", type=int, default=0)
     ap.add_argument("--tile-bins", type=int, default=0)
@@ -271,7 +273,8 @@ def run_ours(args):
     fop = host.cuda()
     fop32 = fop if args.dtype == "f32" else host32.cuda()
     cands = hs.CandBuffer(1 << 20)
-    plan = hs.Plan(nt, n, H, ta, dtype=args.dtype, order=args.order, tile_bins=args.tile_bins)
+    plan = hs.Plan(nt, n, H, ta, dtype=args.dtype, order=args.order, tile_bins=args.tile_bins,
+                   grid_per_sm=args.grid_per_sm)
     stream = torch.cuda.current_stream()
 
     def step():
@@ -355,7 +358,8 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
             "config": {"workload": wl.name, "n_templates": nt, "n_bins": n, "H": H,
                        "p_fa": wl.p_fa, "kernel": plan.kernel, "tile_bins": plan.tile_bins,
-                       "order": args.order, "candidates": n_cand,
+                       "order": args.order, "grid_per_sm": args.grid_per_sm,
+                       "candidates": n_cand,
                        "l2": f"plane {nt * n * es / 1e6:.0f} MB > {L2_BYTES / 1e6:.0f} MB L2: "
                              "inputs larger than L2, no flush",
                        "parallelism": f"{ws} independent planes (one per GPU)"},
@@ -377,10 +381,94 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """64 beams of 85 templates x n_bins (log-uniform in [2^18, 2^22]),
+    H = 16, FP32, summed by one graph-replayed batched launch per step."""
+    import torch
+
+    from paper_1805_12258_gb300 import autotune
+    from paper_1805_12258_gb300 import build as hsbuild
+    from paper_1805_12258_gb300 import hs, synth
+
+    torch.cuda.set_device(0)
+    hsbuild.build()
+    nt, H = 85, 16
+    sizes = [int(x) for x in synth.beam_lengths(args.beams, seed=3)]
+    ta = synth.thresholds(1e-8, H, nt)
+    beams, planes = [], []
+    for i, n in enumerate(sizes):
+        ld = (n + 3) // 4 * 4
+        g = torch.Generator(device="cuda")
+        g.manual_seed(3000 + i)
+        dev = torch.empty((nt, ld), device="cuda").exponential_(generator=g)
+        beams.append((dev, n, hs.CandBuffer(1 << 16)))
+    points = nt * sum(sizes)
+    gps = args.grid_per_sm
+    tuned = None
+    if gps < 0:  # let the autotuner choose
+        best, table = autotune.tune_batch(nt, H, ta, beams)
+        gps = best["grid_per_sm"]
+        tuned = table
+    stream = torch.cuda.current_stream()
+    with hs.Batch(nt, H, ta, grid_per_sm=gps, max_beams=len(beams)) as batch:
+        batch.set_beams(beams)
+        for _ in range(max(3, args.warmup)):
+            batch.graph_run(stream)
+        torch.cuda.synchronize()
+        steps = max(3, min(args.steps, 200))
+        clocks = ClockSampler(0)
+        clocks.start()
+        time.sleep(0.3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            batch.graph_run(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        ms = e0.elapsed_time(e1) / steps
+        n_cand = sum(b[2].sync()[1] for b in beams)
+        tiles = batch.tiles
+    # the same beams one hs_run each, for comparison
+    t_seq = 0.0
+    for dev, n, cb in beams:
+        with hs.Plan(nt, n, H, ta, row_pitch=dev.shape[1]) as plan:
+            plan.run(dev, cb)
+            torch.cuda.synchronize()
+            plan.set_timing(True)
+            plan.kernel_time()
+            plan.run(dev, cb)
+            t, k = plan.kernel_time()
+            t_seq += t
+    algo = nt * sum(sizes) * 4 + H * nt * 4 + 16 * n_cand + 8 * len(beams)
+    peak, kind = peaks()
+    print(json.dumps({
+        "metric": METRIC, "value": points / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (planes generated on the device)",
+        "config": {"workload": f"batch of {len(beams)} beams, 85 templates x n_bins "
+                               "log-uniform in [2^18, 2^22], H=16 fp32",
+                   "beams": len(beams), "bins_total": sum(sizes), "tiles": tiles,
+                   "grid_per_sm": gps, "graph": True, "candidates": n_cand,
+                   "l2": "inputs larger than L2, no flush"},
+        "sequential_hs_run_ms": t_seq, "batch_speedup_vs_sequential": t_seq / ms,
+        "roofline": {"bound": "hbm", "achieved": algo / (ms / 1e3) / 1e9, "peak": peak,
+                     "unit": "GB/s", "frac": algo / (ms / 1e3) / 1e9 / peak, "traffic": None,
+                     "peak_kind": f"{kind} copy bandwidth", "kernel": "batched 85x16 f32",
+                     "algo_bytes_per_launch": algo,
+                     "timed": "CUDA events around each graph replay (counter reset + kernel)"},
+        "autotune": tuned, "e2e": None, "cpu_baseline": None, "clocks": clk,
+        "gpu_launches": 2 * steps,
+    }), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -73,7 +73,10 @@ typedef struct {
     int kernel;     /* hs_kernel: AUTO picks the staged kernel when it applies */
     int tile_bins;  /* bins per CTA of the staged kernel: 0 = default */
     int order;      /* tile order: 0 = default (octave), 1 = linear, 2 = octave-interleaved */
-    int reserved[2];
+    int grid_per_sm;/* staged kernel: 0 = one CTA per tile; k > 0 = k resident CTAs per SM
+                       that walk the tiles */
+    int row_pitch;  /* elements between plane rows (0 = n_bins); >= n_bins.  The staged
+                       kernel needs row_pitch * element size to be a multiple of 16 bytes */
 } hs_options;
 
 /* Candidate record flags */
@@ -118,7 +121,7 @@ HS_API hs_status hs_plan_create(hs_plan **out, int n_templates, int64_t n_bins, 
                          const float *thresholds, const hs_options *opt);
 
 /* Enqueue harmonic summing + detection of one plane on `stream`.
- *  fop   : device plane [n_templates][n_bins], row-major, plan dtype,
+ *  fop   : device plane [n_templates][row pitch], row-major, plan dtype,
  *          16-byte aligned; borrowed until the stream passes the kernel.
  *  cands : caller-owned buffer (see hs_cand_buf).
  * A plan may serve several streams at once if each run has its own cands.
@@ -154,6 +157,54 @@ HS_API hs_status hs_cand_sync(const hs_cand_buf *cands, hs_stream_t stream, uint
 HS_API hs_status hs_run_host(hs_plan *plan, const void *fop_host, void *fop_dev,
                       const hs_cand_buf *cands, hs_cand *host_records,
                       uint32_t host_capacity, hs_stream_t stream, uint32_t *n_out);
+
+/* ---- Batched form: many planes (beams) of one shape in one launch ---------
+ * The paper processes one plane per DM trial and several planes on separate
+ * boards (Section VI-C); a pipeline has thousands per observation.  A batch
+ * sums many planes of the same template count, level count and thresholds,
+ * each with its own number of bins, in one launch over the concatenated tile
+ * list of all beams. */
+typedef struct {
+    const void *fop;     /* device plane [n_templates][ld], 16-byte aligned */
+    const float *fop32;  /* FP32 copy for rechecks (16-bit batches), or NULL */
+    int64_t n_bins;      /* bins of this beam */
+    int64_t ld;          /* row pitch in elements (0 = n_bins); ld * elem a multiple of 16 */
+    hs_cand_buf cands;   /* this beam's candidate buffer (reset by every run) */
+} hs_beam;
+
+typedef struct hs_batch hs_batch;
+
+/* Create a batch for up to max_beams beams (1..65536) of n_templates rows and
+ * H levels with thresholds TA[H][n_templates] (copied).  opt: dtype and
+ * grid_per_sm (0 = one CTA per tile; k > 0 = k resident CTAs per SM).  Compiled shapes: 85 x 16
+ * (FP32, BF16) and 21 x 8 (FP32), stretch index map, symmetric rounding.
+ * Errors: HS_ERR_INVALID, HS_ERR_UNSUPPORTED, HS_ERR_OOM, HS_ERR_CUDA. */
+HS_API hs_status hs_batch_create(hs_batch **out, int n_templates, int H, const float *thresholds,
+                                 const hs_options *opt, int max_beams);
+
+/* Describe the beams of the next runs (host array, copied); uploads the
+ * beam table on `stream`.  The planes and buffers are borrowed until the
+ * stream passes the runs that use them.  Errors: HS_ERR_INVALID, HS_ERR_CUDA. */
+HS_API hs_status hs_batch_set_beams(hs_batch *b, const hs_beam *beams, int n_beams,
+                                    hs_stream_t stream);
+
+/* Enqueue one run over every beam set by hs_batch_set_beams: resets each
+ * beam's counters, then one launch of resident CTAs walks all tiles. */
+HS_API hs_status hs_batch_run(hs_batch *b, hs_stream_t stream);
+
+/* As hs_batch_run, through a CUDA graph captured on first use (on a private
+ * stream) and replayed on `stream`.  The graph reads the beam table from
+ * device memory, so it stays valid when hs_batch_set_beams changes the beams;
+ * it is re-captured when the launch grid (the tile count, with one CTA per
+ * tile) changes. */
+HS_API hs_status hs_batch_graph_run(hs_batch *b, hs_stream_t stream);
+
+/* Tiles of the current beam set. */
+HS_API int hs_batch_tiles(const hs_batch *b);
+
+/* Destroy a batch (NULL is accepted); synchronises the device first. */
+HS_API hs_status hs_batch_destroy(hs_batch *b);
+HS_API const char *hs_batch_last_error(void);
 
 /* Harmonic summing with no device allocation.  The paper has no counterpart:
  * this entry point is for callers that may not allocate device memory, such

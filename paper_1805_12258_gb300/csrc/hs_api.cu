@@ -20,6 +20,7 @@ using namespace hs;
 struct hs_plan {
     int nt = 0;
     long long n = 0;
+    long long ld = 0; // row pitch (elements)
     int H = 0;
     hs_options opt{};
     int device = 0;
@@ -78,29 +79,65 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-// One 2-D descriptor per stretch factor m over the plane [nt][n].
+} // namespace
+
+CUresult hs::encode_tensor_map(CUtensorMap *map, int dtype, const void *base, long long n_bins,
+                               long long ld, int n_templates, int box_w, int box_rows)
+{
+    auto fn = encode_fn();
+    if (!fn)
+        return CUDA_ERROR_NOT_SUPPORTED;
+    const CUtensorMapDataType dt = dtype == HS_F32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : dtype == HS_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    const size_t es = elem_size(dtype);
+    cuuint64_t dims[2] = {(cuuint64_t)n_bins, (cuuint64_t)n_templates};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * es};
+    cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(map, dt, 2, const_cast<void *>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+}
+
+int hs::group_bounds(const float *ta, int n_templates, int H, float delta, float band_abs,
+                     float *out)
+{
+    int ends[kMaxGroups];
+    const int groups = staged_groups(H, ends);
+    int a = 1;
+    for (int g = 0; g < groups; ++g) {
+        double t = INFINITY;
+        for (int k = a; k <= ends[g]; ++k)
+            for (int r = 0; r < n_templates; ++r)
+                t = std::min(t, (double)ta[(size_t)(k - 1) * n_templates + r]);
+        // A hit needs s (1 + delta) > t - band_abs; the fast pass sums a
+        // group in tree order, within 2*gamma_H of the ascending sum, so
+        // the bound is lowered by a further relative H*2^-22 (> 2 gamma_H)
+        double lowered = (t - band_abs) / (1.0 + delta);
+        lowered -= std::fabs(lowered) * H * std::ldexp(1.0, -22);
+        float lf = (float)lowered;
+        if ((double)lf > lowered)
+            lf = std::nextafter(lf, -INFINITY);
+        out[g] = lf;
+        a = ends[g] + 1;
+    }
+    return groups;
+}
+
+namespace {
+
+// The staged kernel's 2-D descriptors over the plane [nt][n], one per
+// stretch factor m.
 hs_status encode_maps(hs_plan *p, const void *fop)
 {
     if (p->map_ptr == fop)
         return HS_OK;
-    auto fn = encode_fn();
-    if (!fn)
-        return fail(HS_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
     const StagedShape sh{p->nt, p->H, p->tb, p->opt.dtype};
-    const CUtensorMapDataType dt = p->opt.dtype == HS_F32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                   : p->opt.dtype == HS_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
-                                                             : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-    const size_t es = elem_size(p->opt.dtype);
     for (int m = 1; m <= p->H; ++m) {
         int w = 0, rows = 0;
         staged_box(sh, m, &w, &rows);
-        cuuint64_t dims[2] = {(cuuint64_t)p->n, (cuuint64_t)p->nt};
-        cuuint64_t strides[1] = {(cuuint64_t)p->n * es};
-        cuuint32_t box[2] = {(cuuint32_t)w, (cuuint32_t)rows};
-        cuuint32_t estr[2] = {1, 1};
-        CUresult r = fn(&p->maps[m - 1], dt, 2, const_cast<void *>(fop), dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        CUresult r = encode_tensor_map(&p->maps[m - 1], p->opt.dtype, fop, p->n, p->ld, p->nt, w, rows);
         if (r != CUDA_SUCCESS) {
             p->map_ptr = nullptr;
             char buf[128];
@@ -183,8 +220,10 @@ hs_status launch_range(hs_plan *p, const void *fop, const float *fop32, cudaStre
         L.counters = c->count;
         L.cap = c->capacity;
         L.n = p->n;
+        L.ld = p->ld;
         L.tile_lo = (int)(f_lo / p->tb);
         L.tile_hi = (int)((f_hi + p->tb - 1) / p->tb);
+        L.grid_per_sm = p->opt.grid_per_sm;
         e = launch_staged(L, s);
         if (e != cudaSuccess)
             return cuda_fail(e, "staged kernel launch");
@@ -195,6 +234,7 @@ hs_status launch_range(hs_plan *p, const void *fop, const float *fop32, cudaStre
         a.dtype = p->opt.dtype;
         a.nt = p->nt;
         a.n = p->n;
+        a.ld = p->ld;
         a.H = p->H;
         a.index = p->opt.index;
         a.zround = p->opt.zround;
@@ -260,8 +300,10 @@ hs_status hs_plan_create(hs_plan **out, int n_templates, int64_t n_bins, int H,
         return fail(HS_ERR_INVALID, "thresholds is null");
     if (o.dtype < HS_F32 || o.dtype > HS_F16 || o.index < 0 || o.index > 1 || o.zround < 0 ||
         o.zround > 1 || o.kernel < 0 || o.kernel > 2 || o.order < 0 || o.order > 2 ||
-        o.tile_bins < 0)
+        o.tile_bins < 0 || o.grid_per_sm < 0 || o.grid_per_sm > 64)
         return fail(HS_ERR_INVALID, "unknown option value");
+    if (o.row_pitch != 0 && o.row_pitch < n_bins)
+        return fail(HS_ERR_INVALID, "row_pitch must be 0 or at least n_bins");
     for (long long i = 0; i < (long long)H * n_templates; ++i)
         if (!std::isfinite(thresholds[i]))
             return fail(HS_ERR_INVALID, "thresholds must be finite");
@@ -271,6 +313,7 @@ hs_status hs_plan_create(hs_plan **out, int n_templates, int64_t n_bins, int H,
         return fail(HS_ERR_OOM, "host allocation of the plan failed");
     p->nt = n_templates;
     p->n = n_bins;
+    p->ld = o.row_pitch ? o.row_pitch : n_bins;
     p->H = H;
     p->opt = o;
     cudaGetDevice(&p->device);
@@ -288,7 +331,7 @@ hs_status hs_plan_create(hs_plan **out, int n_templates, int64_t n_bins, int H,
     p->tb = o.tile_bins ? o.tile_bins : 128;
     const StagedShape sh{n_templates, H, p->tb, o.dtype};
     const bool staged_ok = staged_available(sh) && o.index == HS_INDEX_STRETCH &&
-                           o.zround == HS_ZROUND_SYMMETRIC && (n_bins * es) % 16 == 0;
+                           o.zround == HS_ZROUND_SYMMETRIC && (p->ld * (long long)es) % 16 == 0;
     if (o.kernel == HS_KERNEL_STAGED && !staged_ok) {
         delete p;
         return fail(HS_ERR_UNSUPPORTED, "no staged kernel for this shape/options "
@@ -314,26 +357,9 @@ hs_status hs_plan_create(hs_plan **out, int n_templates, int64_t n_bins, int H,
     }
 
     if (p->kernel == HS_KERNEL_STAGED) {
-        int ends[kMaxGroups];
-        p->groups = staged_groups(H, ends);
-        p->tmin.assign((size_t)p->groups, 0.f);
-        int a = 1;
-        for (int g = 0; g < p->groups; ++g) {
-            double t = INFINITY;
-            for (int k = a; k <= ends[g]; ++k)
-                for (int r = 0; r < n_templates; ++r)
-                    t = std::min(t, (double)p->ta[(size_t)(k - 1) * n_templates + r]);
-            // A hit needs s (1 + delta) > t - band_abs; the fast pass sums a
-            // group in tree order, within 2*gamma_H of the ascending sum, so
-            // the bound is lowered by a further relative H*2^-22 (> 2 gamma_H)
-            double lowered = (t - p->band_abs) / (1.0 + p->delta);
-            lowered -= std::fabs(lowered) * H * std::ldexp(1.0, -22);
-            float lf = (float)lowered;
-            if ((double)lf > lowered)
-                lf = std::nextafter(lf, -INFINITY);
-            p->tmin[g] = lf;
-            a = ends[g] + 1;
-        }
+        p->tmin.assign((size_t)kMaxGroups, 0.f);
+        p->groups = group_bounds(p->ta.data(), n_templates, H, p->delta, p->band_abs,
+                                 p->tmin.data());
         p->n_tiles = (int)((n_bins + p->tb - 1) / p->tb);
         const int kind = o.order == 0 ? 2 : o.order; // default: octave-interleaved
         std::vector<uint32_t> ord = tile_order(p->n_tiles, kind);
@@ -451,7 +477,7 @@ hs_status hs_run_host(hs_plan *p, const void *fop_host, void *fop_dev, const hs_
             if (hi <= prev)
                 continue;
             const size_t off = (size_t)prev * es, width = (size_t)(hi - prev) * es,
-                         pitch = (size_t)p->n * es;
+                         pitch = (size_t)p->ld * es;
             e = cudaMemcpy2DAsync(static_cast<char *>(fop_dev) + off, pitch,
                                   static_cast<const char *>(fop_host) + off, pitch, width,
                                   (size_t)p->nt, cudaMemcpyHostToDevice, p->copy_stream);

@@ -1,0 +1,301 @@
+// hs_batch.cu -- the batched form: many planes (beams) of one shape, each of
+// its own length, summed by one launch over the concatenated tile list of all
+// beams.  The beam descriptors and a tile -> beam table live in device
+// memory, so one captured CUDA graph serves every beam set with the same
+// launch grid (one CTA per tile by default, or a fixed number of resident
+// CTAs per SM); hs_batch_graph_run replays it and re-captures when the grid
+// changes.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hs_internal.h"
+
+using namespace hs;
+
+struct hs_batch {
+    int nt = 0, H = 0, dtype = HS_F32, tb = 128;
+    int max_beams = 0, n_beams = 0, total_tiles = 0;
+    int grid = 0;
+    float delta = 0.f, band_abs = 0.f;
+    std::vector<float> ta;
+    float tmin[kMaxGroups];
+    float *d_ta = nullptr;
+    void *d_beams = nullptr;
+    int *d_header = nullptr;
+    int *d_tile_beam = nullptr; // beam of each tile
+    long long tile_beam_cap = 0;
+    std::vector<unsigned char> h_beams;
+    std::vector<int> h_tile_beam;
+    int h_header[2] = {0, 0};
+    int grid_per_sm = 0;        // 0: one CTA per tile
+    int sms = 0;
+    std::mutex mu;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int graph_grid = 0;         // grid the captured graph was made for
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+hs_status fail(hs_status s, const std::string &msg)
+{
+    g_err = msg;
+    return s;
+}
+
+hs_status cuda_fail(cudaError_t e, const char *what)
+{
+    g_err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return e == cudaErrorMemoryAllocation ? HS_ERR_OOM : HS_ERR_CUDA;
+}
+
+size_t elem_size(int dtype) { return dtype == HS_F32 ? 4 : 2; }
+
+StagedBatch launch_args(const hs_batch *b)
+{
+    StagedBatch a{};
+    a.sh = StagedShape{b->nt, b->H, b->tb, b->dtype};
+    a.tmin_host = b->tmin;
+    a.ta = b->d_ta;
+    a.delta = b->delta;
+    a.band_abs = b->band_abs;
+    a.beams = b->d_beams;
+    a.header = b->d_header;
+    a.tile_beam = b->d_tile_beam;
+    a.max_beams = b->max_beams;
+    a.grid = b->grid_per_sm > 0 ? std::min(b->sms * b->grid_per_sm, std::max(1, b->total_tiles))
+                                : std::max(1, b->total_tiles);
+    return a;
+}
+
+} // namespace
+
+extern "C" {
+
+const char *hs_batch_last_error(void) { return g_err.c_str(); }
+
+hs_status hs_batch_create(hs_batch **out, int n_templates, int H, const float *thresholds,
+                          const hs_options *opt, int max_beams)
+{
+    if (!out)
+        return fail(HS_ERR_INVALID, "out is null");
+    *out = nullptr;
+    hs_options o{};
+    if (opt)
+        o = *opt;
+    if (n_templates < 1 || n_templates % 2 == 0 || n_templates > 32767 || H < 1 || H > 32)
+        return fail(HS_ERR_INVALID, "n_templates must be odd (1..32767) and H in [1, 32]");
+    if (max_beams < 1 || max_beams > (1 << 16))
+        return fail(HS_ERR_INVALID, "max_beams must be in [1, 65536]");
+    if (!thresholds)
+        return fail(HS_ERR_INVALID, "thresholds is null");
+    for (long long i = 0; i < (long long)H * n_templates; ++i)
+        if (!std::isfinite(thresholds[i]))
+            return fail(HS_ERR_INVALID, "thresholds must be finite");
+    if (o.dtype < HS_F32 || o.dtype > HS_F16 || o.grid_per_sm < 0 || o.grid_per_sm > 64)
+        return fail(HS_ERR_INVALID, "unknown option value");
+    const StagedShape sh{n_templates, H, 128, o.dtype};
+    if (!staged_batch_available(sh) || o.index != HS_INDEX_STRETCH ||
+        o.zround != HS_ZROUND_SYMMETRIC)
+        return fail(HS_ERR_UNSUPPORTED, "no batched kernel for this shape/options (compiled: "
+                                        "85x16 FP32/BF16 and 21x8 FP32, stretch, symmetric)");
+    hs_batch *b = new (std::nothrow) hs_batch();
+    if (!b)
+        return fail(HS_ERR_OOM, "host allocation of the batch failed");
+    b->nt = n_templates;
+    b->H = H;
+    b->dtype = o.dtype;
+    b->max_beams = max_beams;
+    b->ta.assign(thresholds, thresholds + (size_t)H * n_templates);
+    if (o.dtype == HS_BF16)
+        b->delta = (float)((std::ldexp(1.0, -8) + H * std::ldexp(1.0, -22)) * 1.01);
+    else if (o.dtype == HS_F16) {
+        b->delta = (float)((std::ldexp(1.0, -11) + H * std::ldexp(1.0, -22)) * 1.01);
+        b->band_abs = (float)(H * std::ldexp(1.0, -24));
+    }
+    group_bounds(b->ta.data(), n_templates, H, b->delta, b->band_abs, b->tmin);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaError_t e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    b->grid_per_sm = o.grid_per_sm;
+    b->h_beams.assign(staged_beam_desc_bytes() * max_beams, 0);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&b->d_ta, sizeof(float) * b->ta.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_ta, b->ta.data(), sizeof(float) * b->ta.size(),
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&b->d_beams, b->h_beams.size());
+    if (e == cudaSuccess)
+        e = cudaMemset(b->d_beams, 0, b->h_beams.size());
+    if (e == cudaSuccess)
+        e = cudaMalloc(&b->d_header, 2 * sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMemset(b->d_header, 0, 2 * sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        hs_batch_destroy(b);
+        return cuda_fail(e, "batch device tables");
+    }
+    *out = b;
+    return HS_OK;
+}
+
+hs_status hs_batch_set_beams(hs_batch *b, const hs_beam *beams, int n_beams, hs_stream_t stream)
+{
+    if (!b || (!beams && n_beams > 0))
+        return fail(HS_ERR_INVALID, "batch or beams is null");
+    if (n_beams < 0 || n_beams > b->max_beams)
+        return fail(HS_ERR_INVALID, "n_beams must be in [0, max_beams]");
+    const size_t es = elem_size(b->dtype), dsz = staged_beam_desc_bytes();
+    const StagedShape sh{b->nt, b->H, b->tb, b->dtype};
+    std::lock_guard<std::mutex> lk(b->mu);
+    long long total = 0;
+    for (int i = 0; i < n_beams; ++i) {
+        const hs_beam &bm = beams[i];
+        const long long ld = bm.ld ? bm.ld : bm.n_bins;
+        if (!bm.fop || reinterpret_cast<uintptr_t>(bm.fop) % 16 != 0 || bm.n_bins < 1 ||
+            bm.n_bins > 0x7fffffffLL || ld < bm.n_bins || (ld * (long long)es) % 16 != 0)
+            return fail(HS_ERR_INVALID, "beam " + std::to_string(i) +
+                                            ": plane must be 16-byte aligned with a row pitch "
+                                            ">= n_bins and a multiple of 16 bytes");
+        if (!bm.cands.count || (bm.cands.capacity > 0 && !bm.cands.records) ||
+            reinterpret_cast<uintptr_t>(bm.cands.records) % 16 != 0)
+            return fail(HS_ERR_INVALID, "beam " + std::to_string(i) + ": bad candidate buffer");
+        if (bm.fop32 && (b->dtype == HS_F32 || reinterpret_cast<uintptr_t>(bm.fop32) % 16 != 0))
+            return fail(HS_ERR_INVALID, "beam " + std::to_string(i) + ": bad FP32 copy");
+        CUtensorMap maps[kMaxStagedH];
+        for (int m = 1; m <= b->H; ++m) {
+            int w = 0, rows = 0;
+            staged_box(sh, m, &w, &rows);
+            CUresult r = encode_tensor_map(&maps[m - 1], b->dtype, bm.fop, bm.n_bins, ld, b->nt,
+                                           w, rows);
+            if (r != CUDA_SUCCESS)
+                return fail(HS_ERR_CUDA, "cuTensorMapEncodeTiled failed for beam " +
+                                             std::to_string(i));
+        }
+        staged_fill_beam_desc(b->h_beams.data() + dsz * i, maps, b->H, bm.fop, bm.fop32,
+                              bm.n_bins, ld, bm.cands, (int)total);
+        total += (bm.n_bins + b->tb - 1) / b->tb;
+        if (total > 0x7fffffffLL)
+            return fail(HS_ERR_INVALID, "batch has more than 2^31 tiles");
+    }
+    b->n_beams = n_beams;
+    b->total_tiles = (int)total;
+    b->h_header[0] = n_beams;
+    b->h_header[1] = (int)total;
+    b->h_tile_beam.resize((size_t)total);
+    {
+        long long t = 0;
+        for (int i = 0; i < n_beams; ++i) {
+            const long long nt_i = (beams[i].n_bins + b->tb - 1) / b->tb;
+            for (long long j = 0; j < nt_i; ++j)
+                b->h_tile_beam[(size_t)(t + j)] = i;
+            t += nt_i;
+        }
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (total > b->tile_beam_cap) {
+        // the old table may still be read by queued runs: wait for them
+        e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) {
+            cudaFree(b->d_tile_beam);
+            b->d_tile_beam = nullptr;
+            b->tile_beam_cap = 0;
+            e = cudaMalloc(&b->d_tile_beam, sizeof(int) * (size_t)total);
+        }
+        if (e != cudaSuccess)
+            return cuda_fail(e, "allocating the tile table");
+        b->tile_beam_cap = total;
+        if (b->gexec) { // the captured graph holds the old table's address
+            cudaGraphExecDestroy(b->gexec);
+            b->gexec = nullptr;
+        }
+    }
+    // pageable sources: the copies complete their host-side read before return
+    if (total > 0)
+        e = cudaMemcpyAsync(b->d_tile_beam, b->h_tile_beam.data(), sizeof(int) * (size_t)total,
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && n_beams > 0)
+        e = cudaMemcpyAsync(b->d_beams, b->h_beams.data(), dsz * n_beams, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_header, b->h_header, sizeof b->h_header, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "uploading the beam table");
+    return HS_OK;
+}
+
+hs_status hs_batch_run(hs_batch *b, hs_stream_t stream)
+{
+    if (!b)
+        return fail(HS_ERR_INVALID, "batch is null");
+    cudaError_t e = launch_staged_batch(launch_args(b), reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? HS_OK : cuda_fail(e, "batched kernel launch");
+}
+
+hs_status hs_batch_graph_run(hs_batch *b, hs_stream_t stream)
+{
+    if (!b)
+        return fail(HS_ERR_INVALID, "batch is null");
+    std::lock_guard<std::mutex> lk(b->mu);
+    cudaError_t e = cudaSuccess;
+    const int grid = launch_args(b).grid;
+    if (b->gexec && b->graph_grid != grid) { // the grid is part of the captured launch
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    if (!b->gexec) {
+        // capture the counter reset and the batched kernel once; they read
+        // the beam table from device memory, so the graph serves any beam set
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const cudaError_t el = launch_staged_batch(launch_args(b), b->cap_stream);
+            e = cudaStreamEndCapture(b->cap_stream, &graph);
+            if (e == cudaSuccess)
+                e = el;
+        }
+        if (e == cudaSuccess)
+            e = cudaGraphInstantiate(&b->gexec, graph, 0);
+        if (graph)
+            cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            b->gexec = nullptr;
+            return cuda_fail(e, "capturing the batch graph");
+        }
+        b->graph_grid = grid;
+    }
+    e = cudaGraphLaunch(b->gexec, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? HS_OK : cuda_fail(e, "cudaGraphLaunch");
+}
+
+int hs_batch_tiles(const hs_batch *b) { return b ? b->total_tiles : 0; }
+
+hs_status hs_batch_destroy(hs_batch *b)
+{
+    if (!b)
+        return HS_OK;
+    cudaDeviceSynchronize();
+    if (b->gexec)
+        cudaGraphExecDestroy(b->gexec);
+    if (b->cap_stream)
+        cudaStreamDestroy(b->cap_stream);
+    cudaFree(b->d_ta);
+    cudaFree(b->d_beams);
+    cudaFree(b->d_header);
+    cudaFree(b->d_tile_beam);
+    delete b;
+    return HS_OK;
+}
+
+} // extern "C"

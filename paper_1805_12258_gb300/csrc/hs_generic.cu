@@ -28,29 +28,29 @@ __device__ __forceinline__ int scale_row(int z, int num, int den, int zround)
 }
 
 template <typename T>
-__device__ __forceinline__ float ld_plane(const T *fop, long long n, int row, long long bin)
+__device__ __forceinline__ float ld_plane(const T *fop, long long ld, int row, long long bin)
 {
-    return to_f32(__ldg(fop + (long long)row * n + bin));
+    return to_f32(__ldg(fop + (long long)row * ld + bin));
 }
 
-// Level value k (1-based) of point (z, f) and the sum of absolute values of
-// its terms.  STRETCH: the cumulative Eq. 2 chain up to k, ascending m;
+// Level value k (1-based) of point (z, f) of a plane with row pitch ld, and
+// the sum of absolute values of its terms.  STRETCH: the cumulative Eq. 2 chain up to k, ascending m;
 // HFRAC: the k terms (z*h/k, f*h/k), ascending h.
 template <typename T>
-__device__ float level_value(const T *fop, int Z, long long n, int index, int zround, int z,
+__device__ float level_value(const T *fop, int Z, long long ld, int index, int zround, int z,
                             long long f, int k, float *abs_sum)
 {
     float s = 0.f, a = 0.f;
     if (index == HS_INDEX_STRETCH) {
         for (int m = 1; m <= k; ++m) {
-            const float v = ld_plane(fop, n, scale_row(z, 1, m, zround) + Z, f / m);
+            const float v = ld_plane(fop, ld, scale_row(z, 1, m, zround) + Z, f / m);
             s = (m == 1) ? v : s + v;
             a += fabsf(v);
         }
     } else {
         for (int h = 1; h <= k; ++h) {
             const float v =
-                ld_plane(fop, n, scale_row(z, h, k, zround) + Z, (f * h) / k);
+                ld_plane(fop, ld, scale_row(z, h, k, zround) + Z, (f * h) / k);
             s = (h == 1) ? v : s + v;
             a += fabsf(v);
         }
@@ -63,7 +63,7 @@ __device__ float level_value(const T *fop, int Z, long long n, int index, int zr
 // *flags set.  For 16-bit planes (delta > 0) a possible hit is re-evaluated
 // from the FP32 copy when one is given.
 template <typename T>
-__device__ bool decide(const T *fop, const float *fop32, int Z, long long n, int index,
+__device__ bool decide(const T *fop, const float *fop32, int Z, long long ld, int index,
                        int zround, int z, long long f, int k, float s, float a, float thr,
                        float delta, float band_abs, float *power, uint32_t *flags)
 {
@@ -77,7 +77,7 @@ __device__ bool decide(const T *fop, const float *fop32, int Z, long long n, int
         if (s == s && s + band < thr) // cannot exceed thr in FP32 (NaN is rechecked)
             return false;
         float a32;
-        const float s32 = level_value(fop32, Z, n, index, zround, z, f, k, &a32);
+        const float s32 = level_value(fop32, Z, ld, index, zround, z, f, k, &a32);
         *power = s32;
         *flags = 0u;
         return s32 > thr;
@@ -107,22 +107,22 @@ __global__ void __launch_bounds__(128)
             float s = 0.f, ab = 0.f;
             for (int m = 1; m <= a.H; ++m) {
                 const float v =
-                    ld_plane(fop, a.n, scale_row(z, 1, m, a.zround) + Z, fc / m);
+                    ld_plane(fop, a.ld, scale_row(z, 1, m, a.zround) + Z, fc / m);
                 s = (m == 1) ? v : s + v;
                 ab += fabsf(v);
                 float pw;
                 uint32_t fl;
-                if (decide(fop, a.fop32, Z, a.n, a.index, a.zround, z, fc, m, s, ab,
+                if (decide(fop, a.fop32, Z, a.ld, a.index, a.zround, z, fc, m, s, ab,
                            __ldg(a.ta + (m - 1) * a.nt + row), a.delta, a.band_abs, &pw, &fl))
                     hits |= 1u << (m - 1);
             }
         } else {
             for (int k = 1; k <= a.H; ++k) {
                 float ab;
-                const float s = level_value(fop, Z, a.n, a.index, a.zround, z, fc, k, &ab);
+                const float s = level_value(fop, Z, a.ld, a.index, a.zround, z, fc, k, &ab);
                 float pw;
                 uint32_t fl;
-                if (decide(fop, a.fop32, Z, a.n, a.index, a.zround, z, fc, k, s, ab,
+                if (decide(fop, a.fop32, Z, a.ld, a.index, a.zround, z, fc, k, s, ab,
                            __ldg(a.ta + (k - 1) * a.nt + row), a.delta, a.band_abs, &pw, &fl))
                     hits |= 1u << (k - 1);
             }
@@ -136,10 +136,10 @@ __global__ void __launch_bounds__(128)
             const int k = __ffs(hits);
             hits &= hits - 1u;
             float ab;
-            const float s = level_value(fop, Z, a.n, a.index, a.zround, z, fc, k, &ab);
+            const float s = level_value(fop, Z, a.ld, a.index, a.zround, z, fc, k, &ab);
             float pw;
             uint32_t fl;
-            decide(fop, a.fop32, Z, a.n, a.index, a.zround, z, fc, k, s, ab,
+            decide(fop, a.fop32, Z, a.ld, a.index, a.zround, z, fc, k, s, ab,
                    __ldg(a.ta + (k - 1) * a.nt + row), a.delta, a.band_abs, &pw, &fl);
             put_record(a.rec, slot++, a.cap, (uint32_t)fc, z, k, fl, pw);
         }

@@ -18,6 +18,7 @@ struct GenericArgs {
     int dtype;            // hs_dtype
     int nt;               // templates (odd)
     long long n;          // bins
+    long long ld;         // row pitch (elements)
     int H;                // levels
     int index;            // hs_index
     int zround;           // hs_zround
@@ -63,9 +64,42 @@ struct StagedLaunch {
     uint32_t *counters;
     uint32_t cap;
     long long n;
+    long long ld;             // row pitch of the plane and its FP32 copy (elements)
     int tile_lo, tile_hi;     // tiles [tile_lo, tile_hi) of the order
+    int grid_per_sm;          // 0: one CTA per tile; k > 0: k resident CTAs per SM
 };
 
 cudaError_t launch_staged(const StagedLaunch &a, cudaStream_t s);
+
+// Batched form: many planes (beams) of one shape in one launch.  The beam
+// table lives in device memory (beams: max_beams descriptors of
+// staged_beam_desc_bytes() each; header: {n_beams, total tiles}).
+struct StagedBatch {
+    StagedShape sh;
+    const float *tmin_host;
+    const float *ta;
+    float delta, band_abs;
+    const void *beams;
+    const int *header;
+    const int *tile_beam;     // beam of each tile of the batch (device)
+    int max_beams;
+    int grid;                 // CTAs of the launch (they walk the tiles grid-stride)
+};
+
+bool staged_batch_available(const StagedShape &sh);
+size_t staged_beam_desc_bytes();
+void staged_fill_beam_desc(void *dst, const CUtensorMap *maps, int H, const void *fop,
+                           const float *fop32, long long n, long long ld, const hs_cand_buf &cb,
+                           int tile_start);
+
+// Shared host helpers (hs_api.cu)
+CUresult encode_tensor_map(CUtensorMap *map, int dtype, const void *base, long long n_bins,
+                           long long ld, int n_templates, int box_w, int box_rows);
+// Prefilter bound of each level group: the smallest threshold of the group
+// over all rows, lowered for 16-bit storage error and for the fast pass's
+// summation order.  Returns the number of groups.
+int group_bounds(const float *ta, int n_templates, int H, float delta, float band_abs,
+                 float *out);
+cudaError_t launch_staged_batch(const StagedBatch &a, cudaStream_t s);
 
 } // namespace hs

@@ -171,6 +171,7 @@ extern "C" hs_status hs_run_noalloc(int n_templates, int64_t n_bins, int H,
         L.counters = cands->count;
         L.cap = cands->capacity;
         L.n = n_bins;
+        L.ld = n_bins;
         L.tile_lo = 0;
         L.tile_hi = (int)((n_bins + tb - 1) / tb);
         e = launch_staged(L, s);
@@ -181,6 +182,7 @@ extern "C" hs_status hs_run_noalloc(int n_templates, int64_t n_bins, int H,
         a.dtype = HS_F32;
         a.nt = n_templates;
         a.n = n_bins;
+        a.ld = n_bins;
         a.H = H;
         a.index = HS_INDEX_STRETCH;
         a.zround = HS_ZROUND_SYMMETRIC;

@@ -114,7 +114,9 @@ struct Params {
     float delta;            // 16-bit storage relative error bound (0 for FP32)
     float band_abs;         // 16-bit storage absolute error bound
     long long n;
+    long long ld;           // row pitch of the FP32 copy (elements)
     int tile_lo;            // first slot of the tile order this launch covers
+    int n_slots;            // tiles of this launch
 };
 
 // Pairwise (tree) sum of cur[LO..HI] with packed adds; depth log2(HI-LO+1).
@@ -142,45 +144,48 @@ __device__ float chain_f32(const float *fop32, int Z, long long n, int z, int f,
     return s;
 }
 
-// CTAs per SM the register budget is sized for
-#ifndef HS_STAGED_MINB
-#define HS_STAGED_MINB 3
-#endif
+// What one tile reads and writes: its plane's descriptors and size, and the
+// candidate buffer its hits go to (one plane for hs_run, a beam of a batch).
+struct TileTarget {
+    const CUtensorMap *maps; // H descriptors (parameter or global space)
+    const float *fop32;      // FP32 copy for rechecks (row pitch ld), or null
+    long long n;             // bins of the plane
+    long long ld;            // row pitch of the FP32 copy, in elements
+    hs_cand *rec;
+    uint32_t *counters;
+    uint32_t cap;
+};
 
+// Issue the H boxes of the tile starting at bin f0 into the stage (thread 0).
 template <int NT, int H, int TB, typename T>
-__global__ void __launch_bounds__(TB, HS_STAGED_MINB * 128 / TB)
-    staged_kernel(const __grid_constant__ Params<NT, H, T> p)
+__device__ __forceinline__ void issue_tile(const TileTarget &tt, int f0, uint32_t sbase,
+                                           uint32_t bar)
+{
+    using C = Cfg<NT, H, TB, T>;
+    mbar_arrive_expect_tx(bar, (uint32_t)C::TX());
+    static_for<1, H + 1>([&](auto M) {
+        constexpr int m = M;
+        const int x = (f0 / m) & ~(C::ALIGN - 1);
+        tma_load_2d(sbase + C::OFF(m), &tt.maps[m - 1], x, C::Z - C::R(m), bar);
+    });
+}
+
+// Wait for the tile's stage (phase `parity` of `bar`), run the fast pass and
+// the slow pass, append the hits to tt's buffer.  Called by every thread of
+// the CTA; returns false (CTA-uniformly) if the stage did not arrive in time.
+template <int NT, int H, int TB, typename T>
+__device__ __forceinline__ bool sum_tile(const Params<NT, H, T> &p, const TileTarget &tt,
+                                         int f0, const unsigned char *smem, uint32_t bar,
+                                         uint32_t parity)
 {
     using C = Cfg<NT, H, TB, T>;
     constexpr int Z = C::Z;
-    extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar_storage;
-
     const int tid = threadIdx.x;
-    const int slot = p.tile_lo + (int)blockIdx.x;
-    const int tile = p.order ? (int)__ldg(p.order + slot) : slot;
-    const int f0 = tile * TB;
-    const uint32_t sbase = smem_addr(smem);
-    const uint32_t bar = smem_addr(&bar_storage);
-
-    if (tid == 0) {
-        static_for<0, H>([&](auto M) { prefetch_tmap(&p.maps[M]); });
-        mbar_init(bar, 1);
-    }
-    __syncthreads();
-    if (tid == 0) {
-        mbar_arrive_expect_tx(bar, (uint32_t)C::TX());
-        static_for<1, H + 1>([&](auto M) {
-            constexpr int m = M;
-            const int x = (f0 / m) & ~(C::ALIGN - 1);
-            tma_load_2d(sbase + C::OFF(m), &p.maps[m - 1], x, Z - C::R(m), bar);
-        });
-    }
 
     // This thread's column in every span, as an element index of the centre
     // row (template z = 0), computed while the copies are in flight.
     const int f = f0 + tid;
-    const bool valid = (long long)f < p.n;
+    const bool valid = (long long)f < tt.n;
     const T *sm = reinterpret_cast<const T *>(smem);
     int bidx[H];
     static_for<0, H>([&](auto M) {
@@ -189,8 +194,8 @@ __global__ void __launch_bounds__(TB, HS_STAGED_MINB * 128 / TB)
         bidx[M] = C::OFF(m) / C::ES + C::R(m) * C::W(m) + col;
     });
 
-    bool ok = mbar_wait_bounded(bar, 0, kWaitLimitNs);
-    ok = __all_sync(0xffffffffu, ok);
+    // CTA-uniform outcome of the bounded wait for the stage
+    const bool ok = __syncthreads_or(!mbar_wait_bounded(bar, parity, kWaitLimitNs)) == 0;
 
     // ---- fast pass: every row pair, group prefilter ------------------------------
     // d = HP_b - bound has its sign bit set exactly when HP_b < bound (IEEE
@@ -242,11 +247,10 @@ __global__ void __launch_bounds__(TB, HS_STAGED_MINB * 128 / TB)
         });
     }
     if (!ok) {
-        if ((tid & 31) == 0)
-            set_status(p.counters, HS_ERR_TIMEOUT);
-        mbar_wait_bounded(bar, 0, kWaitLimitNs); // let copies in flight land
-
-        return;
+        if (tid == 0)
+            set_status(tt.counters, HS_ERR_TIMEOUT);
+        mbar_wait_bounded(bar, parity, kWaitLimitNs); // let copies in flight land
+        return false;
     }
     if (!valid)
         mask = 0ull;
@@ -272,10 +276,10 @@ __global__ void __launch_bounds__(TB, HS_STAGED_MINB * 128 / TB)
             bool hit;
             if (p.delta == 0.f) {
                 hit = acc > thr[M];
-            } else if (p.fop32 != nullptr) {
+            } else if (tt.fop32 != nullptr) {
                 hit = false;
                 if (!(acc == acc && acc + (p.delta * ab + p.band_abs) < thr[M])) {
-                    power = chain_f32(p.fop32, Z, p.n, z, f, m);
+                    power = chain_f32(tt.fop32, Z, tt.ld, z, f, m);
                     hit = power > thr[M];
                 }
             } else {
@@ -286,7 +290,7 @@ __global__ void __launch_bounds__(TB, HS_STAGED_MINB * 128 / TB)
             if (hit) {
                 hits |= 1u << M;
                 if (write)
-                    put_record(p.rec, rslot++, p.cap, (uint32_t)f, z, m, flags, power);
+                    put_record(tt.rec, rslot++, tt.cap, (uint32_t)f, z, m, flags, power);
             }
         });
         return hits;
@@ -304,11 +308,120 @@ __global__ void __launch_bounds__(TB, HS_STAGED_MINB * 128 / TB)
             if (zz > 0)
                 hb = scan(-zz, false, 0u);
         }
-        uint32_t rsl = warp_reserve(p.counters, (uint32_t)(__popc(ht) + __popc(hb)));
+        uint32_t rsl = warp_reserve(tt.counters, (uint32_t)(__popc(ht) + __popc(hb)));
         if (ht)
             scan(zz, true, rsl);
         if (hb)
             scan(-zz, true, rsl + (uint32_t)__popc(ht));
+    }
+    return true;
+}
+
+// CTAs per SM the register budget is sized for
+#ifndef HS_STAGED_MINB
+#define HS_STAGED_MINB 3
+#endif
+
+// One plane.  Grid-stride over the tile order: with one CTA per tile each CTA
+// sums one tile; with a smaller grid the CTAs stay resident and walk several
+// tiles, saving the launch and teardown of a CTA per tile.
+template <int NT, int H, int TB, typename T>
+__global__ void __launch_bounds__(TB, HS_STAGED_MINB * 128 / TB)
+    staged_kernel(const __grid_constant__ Params<NT, H, T> p)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar_storage;
+    const uint32_t sbase = smem_addr(smem);
+    const uint32_t bar = smem_addr(&bar_storage);
+    if (threadIdx.x == 0) {
+        static_for<0, H>([&](auto M) { prefetch_tmap(&p.maps[M]); });
+        mbar_init(bar, 1);
+    }
+    __syncthreads();
+    const TileTarget tt{p.maps, p.fop32, p.n, p.ld, p.rec, p.counters, p.cap};
+    uint32_t parity = 0;
+    for (int i = (int)blockIdx.x; i < p.n_slots; i += (int)gridDim.x, parity ^= 1u) {
+        const int slot = p.tile_lo + i;
+        const int f0 = (p.order ? (int)__ldg(p.order + slot) : slot) * TB;
+        if (threadIdx.x == 0)
+            issue_tile<NT, H, TB, T>(tt, f0, sbase, bar);
+        if (!sum_tile<NT, H, TB, T>(p, tt, f0, smem, bar, parity))
+            break;
+        __syncthreads(); // the stage is free before the next tile's boxes land
+    }
+}
+
+// One beam of a batch, in device memory: its descriptors, size, output and
+// first tile in the concatenated tile list of the batch.
+struct alignas(128) BeamDesc {
+    CUtensorMap maps[kMaxStagedH];
+    const void *fop;
+    const float *fop32;
+    long long n;
+    long long ld;
+    hs_cand *rec;
+    uint32_t *counters;
+    uint32_t cap;
+    int tile_start;
+};
+
+// Many beams in one launch: the CTAs walk the concatenated tile list of all
+// beams grid-stride (one tile per CTA when the grid covers the list); the
+// beam of each tile comes from a table, and the beam count, tile count and
+// beam descriptors from device memory, so a captured launch serves any beam
+// set of the same tile count.
+template <int NT, int H, int TB, typename T>
+__global__ void __launch_bounds__(TB, HS_STAGED_MINB * 128 / TB)
+    batched_kernel(const __grid_constant__ Params<NT, H, T> p, const BeamDesc *__restrict__ beams,
+                   const int *__restrict__ header /* n_beams, total tiles */,
+                   const int *__restrict__ tile_beam)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar_storage;
+    __shared__ int cur_beam, cur_tile;
+    const uint32_t sbase = smem_addr(smem);
+    const uint32_t bar = smem_addr(&bar_storage);
+    if (threadIdx.x == 0)
+        mbar_init(bar, 1);
+    __syncthreads();
+    const int total = __ldg(header + 1);
+    int last_beam = -1; // beam whose descriptors thread 0 last fenced
+    uint32_t parity = 0;
+    for (int i = (int)blockIdx.x; i < total; i += (int)gridDim.x, parity ^= 1u) {
+        if (threadIdx.x == 0) {
+            const int b = __ldg(tile_beam + i);
+            const BeamDesc &d = beams[b];
+            const int tile = i - d.tile_start;
+            if (b != last_beam) { // descriptors written by the host before the launch
+                static_for<0, H>([&](auto M) {
+                    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                                     reinterpret_cast<uint64_t>(&d.maps[M]))
+                                 : "memory");
+                });
+                last_beam = b;
+            }
+            cur_beam = b;
+            cur_tile = tile;
+            const TileTarget tt{d.maps, d.fop32, d.n, d.ld, d.rec, d.counters, d.cap};
+            issue_tile<NT, H, TB, T>(tt, tile * TB, sbase, bar);
+        }
+        __syncthreads();
+        const BeamDesc &d = beams[cur_beam];
+        const TileTarget tt{d.maps, d.fop32, d.n, d.ld, d.rec, d.counters, d.cap};
+        if (!sum_tile<NT, H, TB, T>(p, tt, cur_tile * TB, smem, bar, parity))
+            break;
+        __syncthreads();
+    }
+}
+
+// Reset the candidate counters of every beam of a batch.
+__global__ void reset_beam_counters(const BeamDesc *beams, const int *header)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < __ldg(header)) {
+        uint32_t *c = beams[b].counters;
+        c[0] = 0u;
+        c[1] = 0u;
     }
 }
 
@@ -330,9 +443,10 @@ cudaError_t launch_one(const StagedLaunch &a, cudaStream_t s)
     p.delta = a.delta;
     p.band_abs = a.band_abs;
     p.n = a.n;
+    p.ld = a.ld;
     p.tile_lo = a.tile_lo;
-    const int tiles = a.tile_hi - a.tile_lo;
-    if (tiles <= 0)
+    p.n_slots = a.tile_hi - a.tile_lo;
+    if (p.n_slots <= 0)
         return cudaSuccess;
     auto kern = staged_kernel<NT, H, TB, T>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
@@ -340,7 +454,42 @@ cudaError_t launch_one(const StagedLaunch &a, cudaStream_t s)
         e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess)
         return e;
-    kern<<<tiles, TB, C::SMEM, s>>>(p);
+    int grid = p.n_slots;
+    if (a.grid_per_sm > 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess)
+            return e;
+        grid = sms * a.grid_per_sm < grid ? sms * a.grid_per_sm : grid;
+    }
+    kern<<<grid, TB, C::SMEM, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <int NT, int H, int TB, typename T>
+cudaError_t launch_batch_one(const StagedBatch &a, cudaStream_t s)
+{
+    using C = Cfg<NT, H, TB, T>;
+    Params<NT, H, T> p;
+    std::memset(&p, 0, sizeof p);
+    for (int g = 0; g < C::G; ++g)
+        p.tmin[g] = a.tmin_host[g];
+    p.ta = a.ta;
+    p.delta = a.delta;
+    p.band_abs = a.band_abs;
+    const BeamDesc *beams = static_cast<const BeamDesc *>(a.beams);
+    reset_beam_counters<<<(a.max_beams + 127) / 128, 128, 0, s>>>(beams, a.header);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    auto kern = batched_kernel<NT, H, TB, T>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess)
+        return e;
+    kern<<<a.grid, TB, C::SMEM, s>>>(p, beams, a.header, a.tile_beam);
     return cudaGetLastError();
 }
 
@@ -363,6 +512,12 @@ void box_of(int m, int *w, int *rows)
     X(21, 8, 128, float, HS_F32)                                                              \
     X(21, 8, 128, __nv_bfloat16, HS_BF16)                                                     \
     X(21, 8, 128, __half, HS_F16)
+
+// Shapes with a batched kernel (tile width 128).
+#define HS_BATCH_SHAPES(X)                                                                    \
+    X(85, 16, 128, float, HS_F32)                                                             \
+    X(85, 16, 128, __nv_bfloat16, HS_BF16)                                                    \
+    X(21, 8, 128, float, HS_F32)
 
 } // namespace
 
@@ -396,6 +551,47 @@ void staged_box(const StagedShape &sh, int m, int *width, int *rows)
     }
     HS_STAGED_SHAPES(X)
 #undef X
+}
+
+size_t staged_beam_desc_bytes() { return sizeof(BeamDesc); }
+
+void staged_fill_beam_desc(void *dst, const CUtensorMap *maps, int H, const void *fop,
+                           const float *fop32, long long n, long long ld, const hs_cand_buf &cb,
+                           int tile_start)
+{
+    BeamDesc d;
+    std::memset(&d, 0, sizeof d);
+    std::memcpy(d.maps, maps, sizeof(CUtensorMap) * H);
+    d.fop = fop;
+    d.fop32 = fop32;
+    d.n = n;
+    d.ld = ld;
+    d.rec = cb.records;
+    d.counters = cb.count;
+    d.cap = cb.capacity;
+    d.tile_start = tile_start;
+    std::memcpy(dst, &d, sizeof d);
+}
+
+bool staged_batch_available(const StagedShape &sh)
+{
+#define X(NT_, H_, TB_, T_, DT_)                                                              \
+    if (sh.nt == NT_ && sh.H == H_ && sh.tb == TB_ && sh.dtype == DT_)                       \
+        return true;
+    HS_BATCH_SHAPES(X)
+#undef X
+    return false;
+}
+
+cudaError_t launch_staged_batch(const StagedBatch &a, cudaStream_t s)
+{
+    const StagedShape &sh = a.sh;
+#define X(NT_, H_, TB_, T_, DT_)                                                              \
+    if (sh.nt == NT_ && sh.H == H_ && sh.tb == TB_ && sh.dtype == DT_)                       \
+        return launch_batch_one<NT_, H_, TB_, T_>(a, s);
+    HS_BATCH_SHAPES(X)
+#undef X
+    return cudaErrorInvalidValue;
 }
 
 int staged_groups(int H, int *ends)

@@ -47,7 +47,7 @@ class HsError(RuntimeError):
 class hs_options(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int), ("index", ctypes.c_int), ("zround", ctypes.c_int),
                 ("kernel", ctypes.c_int), ("tile_bins", ctypes.c_int), ("order", ctypes.c_int),
-                ("reserved", ctypes.c_int * 2)]
+                ("grid_per_sm", ctypes.c_int), ("row_pitch", ctypes.c_int)]
 
 
 class hs_cand(ctypes.Structure):
@@ -59,6 +59,11 @@ class hs_cand(ctypes.Structure):
 class hs_cand_buf(ctypes.Structure):
     _fields_ = [("records", ctypes.c_void_p), ("count", ctypes.c_void_p),
                 ("capacity", ctypes.c_uint32)]
+
+
+class hs_beam(ctypes.Structure):
+    _fields_ = [("fop", ctypes.c_void_p), ("fop32", ctypes.c_void_p), ("n_bins", ctypes.c_int64),
+                ("ld", ctypes.c_int64), ("cands", hs_cand_buf)]
 
 
 _lib = None
@@ -93,6 +98,18 @@ def lib():
     L.hs_plan_set_timing.argtypes = [vp, i32]
     L.hs_plan_kernel_time.argtypes = [vp, P(ctypes.c_double), P(i32)]
     L.hs_pack_paper.argtypes = [P(hs_cand), i32, P(u32), P(ctypes.c_float)]
+    L.hs_batch_create.argtypes = [P(vp), i32, i32, vp, P(hs_options), i32]
+    L.hs_batch_set_beams.argtypes = [vp, P(hs_beam), i32, vp]
+    L.hs_batch_run.argtypes = [vp, vp]
+    L.hs_batch_graph_run.argtypes = [vp, vp]
+    L.hs_batch_destroy.argtypes = [vp]
+    L.hs_batch_tiles.argtypes = [vp]
+    L.hs_batch_tiles.restype = i32
+    L.hs_batch_last_error.argtypes = []
+    L.hs_batch_last_error.restype = ctypes.c_char_p
+    for name in ("hs_batch_create", "hs_batch_set_beams", "hs_batch_run", "hs_batch_graph_run",
+                 "hs_batch_destroy"):
+        getattr(L, name).restype = i32
     L.hs_run_noalloc.argtypes = [i32, i64, i32, vp, vp, vp, P(hs_cand_buf)]
     L.hs_run_noalloc.restype = i32
     L.hs_noalloc_last_error.argtypes = []
@@ -265,9 +282,10 @@ class Plan:
     """An hs_plan for one plane shape, threshold table and option set."""
 
     def __init__(self, n_templates, n_bins, H, thresholds, *, dtype="f32", index="stretch",
-                 zround="symmetric", kernel="auto", tile_bins=0, order=0):
+                 zround="symmetric", kernel="auto", tile_bins=0, order=0, grid_per_sm=0,
+                 row_pitch=0):
         opt = hs_options(DTYPES[dtype], INDEX[index], ZROUND[zround], KERNELS[kernel],
-                         int(tile_bins), int(order))
+                         int(tile_bins), int(order), int(grid_per_sm), int(row_pitch))
         self.n_templates, self.n_bins, self.H = n_templates, n_bins, H
         self.dtype = dtype
         self.handle = hs_plan_create(n_templates, n_bins, H, thresholds, opt)
@@ -299,6 +317,74 @@ class Plan:
     def close(self):
         if getattr(self, "handle", None):
             hs_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+# ---- batched form --------------------------------------------------------------
+
+def _batch_check(status, what):
+    if status != HS_OK:
+        raise HsError(status, f"{what}: {lib().hs_batch_last_error().decode()}")
+    return status
+
+
+class Batch:
+    """An hs_batch: many planes of one shape (each with its own bin count)
+    summed by one launch over all their tiles; graph_run replays a captured
+    CUDA graph of that launch."""
+
+    def __init__(self, n_templates, H, thresholds, *, dtype="f32", grid_per_sm=0,
+                 max_beams=64):
+        ta = np.ascontiguousarray(thresholds, dtype=np.float32)
+        if ta.shape != (H, n_templates):
+            raise ValueError(f"thresholds must have shape {(H, n_templates)}, got {ta.shape}")
+        opt = hs_options(DTYPES[dtype], 0, 0, 0, 0, 0, int(grid_per_sm), 0)
+        out = ctypes.c_void_p()
+        _batch_check(lib().hs_batch_create(ctypes.byref(out), n_templates, H, ta.ctypes.data,
+                                           ctypes.byref(opt), int(max_beams)), "hs_batch_create")
+        self.handle = out.value
+        self.n_templates, self.H = n_templates, H
+        self._keep = []
+
+    def set_beams(self, beams, stream=None):
+        """beams: list of (fop tensor [n_templates][ld], n_bins, CandBuffer) or
+        (fop, n_bins, CandBuffer, fop32)."""
+        arr = (hs_beam * max(1, len(beams)))()
+        for i, b in enumerate(beams):
+            fop, n_bins, cb = b[0], b[1], b[2]
+            fop32 = b[3] if len(b) > 3 else None
+            ld = fop.shape[-1]
+            arr[i] = hs_beam(_ptr(fop), _ptr(fop32), int(n_bins), int(ld), cb.c)
+        self._keep = list(beams)
+        _batch_check(lib().hs_batch_set_beams(self.handle, arr, len(beams),
+                                              _stream_handle(stream)), "hs_batch_set_beams")
+
+    @property
+    def tiles(self):
+        return lib().hs_batch_tiles(self.handle)
+
+    def run(self, stream=None):
+        _batch_check(lib().hs_batch_run(self.handle, _stream_handle(stream)), "hs_batch_run")
+
+    def graph_run(self, stream=None):
+        _batch_check(lib().hs_batch_graph_run(self.handle, _stream_handle(stream)),
+                     "hs_batch_graph_run")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().hs_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
