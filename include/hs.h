@@ -158,12 +158,14 @@ HS_API hs_status hs_run_host(hs_plan *plan, const void *fop_host, void *fop_dev,
                       const hs_cand_buf *cands, hs_cand *host_records,
                       uint32_t host_capacity, hs_stream_t stream, uint32_t *n_out);
 
-/* ---- Batched form: many planes (beams) of one shape in one launch ---------
+/* ---- Batched form: many planes (beams) of one shape -------------------------
  * The paper processes one plane per DM trial and several planes on separate
  * boards (Section VI-C); a pipeline has thousands per observation.  A batch
  * sums many planes of the same template count, level count and thresholds,
- * each with its own number of bins, in one launch over the concatenated tile
- * list of all beams. */
+ * each with its own number of bins and row pitch.  Each launch carries the
+ * TMA descriptors of up to K beams in its parameter block (K = 15 for the
+ * 85 x 16 shape, 30 for 21 x 8) and covers the concatenated tiles of its
+ * beams; a run issues ceil(n_beams / K) launches after one counter reset. */
 typedef struct {
     const void *fop;     /* device plane [n_templates][ld], 16-byte aligned */
     const float *fop32;  /* FP32 copy for rechecks (16-bit batches), or NULL */
@@ -175,32 +177,37 @@ typedef struct {
 typedef struct hs_batch hs_batch;
 
 /* Create a batch for up to max_beams beams (1..65536) of n_templates rows and
- * H levels with thresholds TA[H][n_templates] (copied).  opt: dtype and
- * grid_per_sm (0 = one CTA per tile; k > 0 = k resident CTAs per SM).  Compiled shapes: 85 x 16
- * (FP32, BF16) and 21 x 8 (FP32), stretch index map, symmetric rounding.
+ * H levels with thresholds TA[H][n_templates] (copied).  opt: dtype, order
+ * (tile order inside each beam, as for a plan) and grid_per_sm (0 = one CTA
+ * per tile; k > 0 = k resident CTAs per SM).  Compiled shapes: 85 x 16 (FP32,
+ * BF16) and 21 x 8 (FP32), stretch index map, symmetric rounding.
  * Errors: HS_ERR_INVALID, HS_ERR_UNSUPPORTED, HS_ERR_OOM, HS_ERR_CUDA. */
 HS_API hs_status hs_batch_create(hs_batch **out, int n_templates, int H, const float *thresholds,
                                  const hs_options *opt, int max_beams);
 
-/* Describe the beams of the next runs (host array, copied); uploads the
- * beam table on `stream`.  The planes and buffers are borrowed until the
- * stream passes the runs that use them.  Errors: HS_ERR_INVALID, HS_ERR_CUDA. */
+/* Describe the beams of the next runs (host array, copied): encodes their
+ * descriptors on the host and uploads their tile order on `stream`.  The
+ * planes and buffers are borrowed until the stream passes the runs that use
+ * them.  On error the previous beam set stays in place.
+ * Errors: HS_ERR_INVALID, HS_ERR_CUDA, HS_ERR_OOM. */
 HS_API hs_status hs_batch_set_beams(hs_batch *b, const hs_beam *beams, int n_beams,
                                     hs_stream_t stream);
 
-/* Enqueue one run over every beam set by hs_batch_set_beams: resets each
- * beam's counters, then one launch of resident CTAs walks all tiles. */
+/* Enqueue one run over every beam set by hs_batch_set_beams: one kernel
+ * clears each beam's counters, then hs_batch_launches() launches sum the
+ * tiles.  Records go to each beam's buffer in an unspecified order. */
 HS_API hs_status hs_batch_run(hs_batch *b, hs_stream_t stream);
 
-/* As hs_batch_run, through a CUDA graph captured on first use (on a private
- * stream) and replayed on `stream`.  The graph reads the beam table from
- * device memory, so it stays valid when hs_batch_set_beams changes the beams;
- * it is re-captured when the launch grid (the tile count, with one CTA per
- * tile) changes. */
+/* As hs_batch_run, through a CUDA graph of the same launches, captured (on
+ * a private stream) on first use and again after hs_batch_set_beams, then
+ * replayed on `stream`; a re-capture updates the instantiated graph in place
+ * when the launch count is unchanged. */
 HS_API hs_status hs_batch_graph_run(hs_batch *b, hs_stream_t stream);
 
-/* Tiles of the current beam set. */
+/* Tiles of the current beam set, and the kernel launches a run issues to
+ * sum them (the counter reset not included). */
 HS_API int hs_batch_tiles(const hs_batch *b);
+HS_API int hs_batch_launches(const hs_batch *b);
 
 /* Destroy a batch (NULL is accepted); synchronises the device first. */
 HS_API hs_status hs_batch_destroy(hs_batch *b);

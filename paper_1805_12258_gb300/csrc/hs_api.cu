@@ -125,6 +125,26 @@ int hs::group_bounds(const float *ta, int n_templates, int H, float delta, float
     return groups;
 }
 
+namespace hs {
+std::vector<uint32_t> tile_order(int n_tiles, int kind)
+{
+    std::vector<uint32_t> o(n_tiles);
+    for (int t = 0; t < n_tiles; ++t)
+        o[t] = (uint32_t)t;
+    if (kind == 2) {
+        auto key = [](uint32_t t) {
+            if (t == 0)
+                return std::make_pair(1.0, -1);
+            int e = 31 - __builtin_clz(t);
+            return std::make_pair((double)t / (double)(1u << e), e);
+        };
+        std::stable_sort(o.begin(), o.end(),
+                         [&](uint32_t a, uint32_t b) { return key(a) < key(b); });
+    }
+    return o;
+}
+} // namespace hs
+
 namespace {
 
 // The staged kernel's 2-D descriptors over the plane [nt][n], one per
@@ -152,24 +172,6 @@ hs_status encode_maps(hs_plan *p, const void *fop)
 // Tile order: linear, or octave-interleaved (tiles sorted by the mantissa of
 // their index, then by octave) so that the tiles reading a span at f/2, f/4,
 // ... run close in time to the tile that reads it at f.
-std::vector<uint32_t> tile_order(int n_tiles, int kind)
-{
-    std::vector<uint32_t> o(n_tiles);
-    for (int t = 0; t < n_tiles; ++t)
-        o[t] = (uint32_t)t;
-    if (kind == 2) {
-        auto key = [](uint32_t t) {
-            if (t == 0)
-                return std::make_pair(1.0, -1);
-            int e = 31 - __builtin_clz(t);
-            return std::make_pair((double)t / (double)(1u << e), e);
-        };
-        std::stable_sort(o.begin(), o.end(),
-                         [&](uint32_t a, uint32_t b) { return key(a) < key(b); });
-    }
-    return o;
-}
-
 hs_status check_cands(const hs_cand_buf *c)
 {
     if (!c || !c->count)

@@ -1,10 +1,9 @@
 // hs_batch.cu -- the batched form: many planes (beams) of one shape, each of
-// its own length, summed by one launch over the concatenated tile list of all
-// beams.  The beam descriptors and a tile -> beam table live in device
-// memory, so one captured CUDA graph serves every beam set with the same
-// launch grid (one CTA per tile by default, or a fixed number of resident
-// CTAs per SM); hs_batch_graph_run replays it and re-captures when the grid
-// changes.
+// its own length and row pitch, summed by a few launches that each carry up
+// to K beams' TMA descriptors in their parameter block (K = 15 for the
+// 85 x 16 shape).  hs_batch_set_beams encodes the descriptors and uploads the
+// per-beam tile order; hs_batch_run launches; hs_batch_graph_run replays a
+// CUDA graph of the same launches, captured again after the beams change.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -19,26 +18,22 @@
 using namespace hs;
 
 struct hs_batch {
-    int nt = 0, H = 0, dtype = HS_F32, tb = 128;
-    int max_beams = 0, n_beams = 0, total_tiles = 0;
-    int grid = 0;
+    int nt = 0, H = 0, dtype = HS_F32, tb = 128, order = 2;
+    int max_beams = 0, total_tiles = 0;
     float delta = 0.f, band_abs = 0.f;
     std::vector<float> ta;
     float tmin[kMaxGroups];
     float *d_ta = nullptr;
-    void *d_beams = nullptr;
-    int *d_header = nullptr;
-    int *d_tile_beam = nullptr; // beam of each tile
-    long long tile_beam_cap = 0;
-    std::vector<unsigned char> h_beams;
-    std::vector<int> h_tile_beam;
-    int h_header[2] = {0, 0};
-    int grid_per_sm = 0;        // 0: one CTA per tile
+    std::vector<StagedBatchBeam> beams;
+    uint32_t *d_order = nullptr; // tile order of each beam, concatenated
+    long long order_cap = 0;
+    std::vector<uint32_t> h_order;
+    int grid_per_sm = 0;         // 0: one CTA per tile
     int sms = 0;
     std::mutex mu;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
-    int graph_grid = 0;         // grid the captured graph was made for
+    bool graph_stale = true;     // beams changed since the graph was captured
 };
 
 namespace {
@@ -67,12 +62,11 @@ StagedBatch launch_args(const hs_batch *b)
     a.ta = b->d_ta;
     a.delta = b->delta;
     a.band_abs = b->band_abs;
-    a.beams = b->d_beams;
-    a.header = b->d_header;
-    a.tile_beam = b->d_tile_beam;
-    a.max_beams = b->max_beams;
-    a.grid = b->grid_per_sm > 0 ? std::min(b->sms * b->grid_per_sm, std::max(1, b->total_tiles))
-                                : std::max(1, b->total_tiles);
+    a.beams = b->beams.data();
+    a.n_beams = (int)b->beams.size();
+    a.order = b->order == 1 ? nullptr : b->d_order;
+    a.grid_per_sm = b->grid_per_sm;
+    a.sms = b->sms;
     return a;
 }
 
@@ -100,7 +94,8 @@ hs_status hs_batch_create(hs_batch **out, int n_templates, int H, const float *t
     for (long long i = 0; i < (long long)H * n_templates; ++i)
         if (!std::isfinite(thresholds[i]))
             return fail(HS_ERR_INVALID, "thresholds must be finite");
-    if (o.dtype < HS_F32 || o.dtype > HS_F16 || o.grid_per_sm < 0 || o.grid_per_sm > 64)
+    if (o.dtype < HS_F32 || o.dtype > HS_F16 || o.grid_per_sm < 0 || o.grid_per_sm > 64 ||
+        o.order < 0 || o.order > 2)
         return fail(HS_ERR_INVALID, "unknown option value");
     const StagedShape sh{n_templates, H, 128, o.dtype};
     if (!staged_batch_available(sh) || o.index != HS_INDEX_STRETCH ||
@@ -113,6 +108,7 @@ hs_status hs_batch_create(hs_batch **out, int n_templates, int H, const float *t
     b->nt = n_templates;
     b->H = H;
     b->dtype = o.dtype;
+    b->order = o.order == 0 ? 2 : o.order;
     b->max_beams = max_beams;
     b->ta.assign(thresholds, thresholds + (size_t)H * n_templates);
     if (o.dtype == HS_BF16)
@@ -126,20 +122,11 @@ hs_status hs_batch_create(hs_batch **out, int n_templates, int H, const float *t
     cudaGetDevice(&dev);
     cudaError_t e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
     b->grid_per_sm = o.grid_per_sm;
-    b->h_beams.assign(staged_beam_desc_bytes() * max_beams, 0);
     if (e == cudaSuccess)
         e = cudaMalloc(&b->d_ta, sizeof(float) * b->ta.size());
     if (e == cudaSuccess)
         e = cudaMemcpy(b->d_ta, b->ta.data(), sizeof(float) * b->ta.size(),
                        cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMalloc(&b->d_beams, b->h_beams.size());
-    if (e == cudaSuccess)
-        e = cudaMemset(b->d_beams, 0, b->h_beams.size());
-    if (e == cudaSuccess)
-        e = cudaMalloc(&b->d_header, 2 * sizeof(int));
-    if (e == cudaSuccess)
-        e = cudaMemset(b->d_header, 0, 2 * sizeof(int));
     if (e == cudaSuccess)
         e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
@@ -156,9 +143,9 @@ hs_status hs_batch_set_beams(hs_batch *b, const hs_beam *beams, int n_beams, hs_
         return fail(HS_ERR_INVALID, "batch or beams is null");
     if (n_beams < 0 || n_beams > b->max_beams)
         return fail(HS_ERR_INVALID, "n_beams must be in [0, max_beams]");
-    const size_t es = elem_size(b->dtype), dsz = staged_beam_desc_bytes();
+    const size_t es = elem_size(b->dtype);
     const StagedShape sh{b->nt, b->H, b->tb, b->dtype};
-    std::lock_guard<std::mutex> lk(b->mu);
+    std::vector<StagedBatchBeam> nb((size_t)n_beams);
     long long total = 0;
     for (int i = 0; i < n_beams; ++i) {
         const hs_beam &bm = beams[i];
@@ -173,65 +160,62 @@ hs_status hs_batch_set_beams(hs_batch *b, const hs_beam *beams, int n_beams, hs_
             return fail(HS_ERR_INVALID, "beam " + std::to_string(i) + ": bad candidate buffer");
         if (bm.fop32 && (b->dtype == HS_F32 || reinterpret_cast<uintptr_t>(bm.fop32) % 16 != 0))
             return fail(HS_ERR_INVALID, "beam " + std::to_string(i) + ": bad FP32 copy");
-        CUtensorMap maps[kMaxStagedH];
+        StagedBatchBeam &d = nb[(size_t)i];
+        std::memset(&d, 0, sizeof d);
         for (int m = 1; m <= b->H; ++m) {
             int w = 0, rows = 0;
             staged_box(sh, m, &w, &rows);
-            CUresult r = encode_tensor_map(&maps[m - 1], b->dtype, bm.fop, bm.n_bins, ld, b->nt,
+            CUresult r = encode_tensor_map(&d.maps[m - 1], b->dtype, bm.fop, bm.n_bins, ld, b->nt,
                                            w, rows);
             if (r != CUDA_SUCCESS)
                 return fail(HS_ERR_CUDA, "cuTensorMapEncodeTiled failed for beam " +
                                              std::to_string(i));
         }
-        staged_fill_beam_desc(b->h_beams.data() + dsz * i, maps, b->H, bm.fop, bm.fop32,
-                              bm.n_bins, ld, bm.cands, (int)total);
-        total += (bm.n_bins + b->tb - 1) / b->tb;
+        d.fop32 = bm.fop32;
+        d.n = bm.n_bins;
+        d.ld = ld;
+        d.rec = bm.cands.records;
+        d.counters = bm.cands.count;
+        d.cap = bm.cands.capacity;
+        d.tiles = (int)((bm.n_bins + b->tb - 1) / b->tb);
+        total += d.tiles;
         if (total > 0x7fffffffLL)
             return fail(HS_ERR_INVALID, "batch has more than 2^31 tiles");
     }
-    b->n_beams = n_beams;
-    b->total_tiles = (int)total;
-    b->h_header[0] = n_beams;
-    b->h_header[1] = (int)total;
-    b->h_tile_beam.resize((size_t)total);
-    {
-        long long t = 0;
-        for (int i = 0; i < n_beams; ++i) {
-            const long long nt_i = (beams[i].n_bins + b->tb - 1) / b->tb;
-            for (long long j = 0; j < nt_i; ++j)
-                b->h_tile_beam[(size_t)(t + j)] = i;
-            t += nt_i;
-        }
-    }
+    std::lock_guard<std::mutex> lk(b->mu);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSuccess;
-    if (total > b->tile_beam_cap) {
-        // the old table may still be read by queued runs: wait for them
-        e = cudaStreamSynchronize(s);
-        if (e == cudaSuccess) {
-            cudaFree(b->d_tile_beam);
-            b->d_tile_beam = nullptr;
-            b->tile_beam_cap = 0;
-            e = cudaMalloc(&b->d_tile_beam, sizeof(int) * (size_t)total);
+    if (b->order != 1) {
+        b->h_order.resize((size_t)total);
+        size_t at = 0;
+        for (const StagedBatchBeam &d : nb) {
+            const std::vector<uint32_t> o = tile_order(d.tiles, b->order);
+            std::copy(o.begin(), o.end(), b->h_order.begin() + (long)at);
+            at += o.size();
         }
+        if (total > b->order_cap) {
+            // the old table may still be read by queued runs: wait for them
+            e = cudaStreamSynchronize(s);
+            if (e == cudaSuccess) {
+                cudaFree(b->d_order);
+                b->d_order = nullptr;
+                b->order_cap = 0;
+                e = cudaMalloc(&b->d_order, sizeof(uint32_t) * (size_t)total);
+            }
+            if (e != cudaSuccess)
+                return cuda_fail(e, "allocating the tile order table");
+            b->order_cap = total;
+        }
+        // pageable source: the copy completes its host-side read before return
+        if (total > 0)
+            e = cudaMemcpyAsync(b->d_order, b->h_order.data(), sizeof(uint32_t) * (size_t)total,
+                                cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess)
-            return cuda_fail(e, "allocating the tile table");
-        b->tile_beam_cap = total;
-        if (b->gexec) { // the captured graph holds the old table's address
-            cudaGraphExecDestroy(b->gexec);
-            b->gexec = nullptr;
-        }
+            return cuda_fail(e, "uploading the tile order");
     }
-    // pageable sources: the copies complete their host-side read before return
-    if (total > 0)
-        e = cudaMemcpyAsync(b->d_tile_beam, b->h_tile_beam.data(), sizeof(int) * (size_t)total,
-                            cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && n_beams > 0)
-        e = cudaMemcpyAsync(b->d_beams, b->h_beams.data(), dsz * n_beams, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->d_header, b->h_header, sizeof b->h_header, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess)
-        return cuda_fail(e, "uploading the beam table");
+    b->beams.swap(nb);
+    b->total_tiles = (int)total;
+    b->graph_stale = true;
     return HS_OK;
 }
 
@@ -239,6 +223,7 @@ hs_status hs_batch_run(hs_batch *b, hs_stream_t stream)
 {
     if (!b)
         return fail(HS_ERR_INVALID, "batch is null");
+    std::lock_guard<std::mutex> lk(b->mu);
     cudaError_t e = launch_staged_batch(launch_args(b), reinterpret_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? HS_OK : cuda_fail(e, "batched kernel launch");
 }
@@ -249,14 +234,9 @@ hs_status hs_batch_graph_run(hs_batch *b, hs_stream_t stream)
         return fail(HS_ERR_INVALID, "batch is null");
     std::lock_guard<std::mutex> lk(b->mu);
     cudaError_t e = cudaSuccess;
-    const int grid = launch_args(b).grid;
-    if (b->gexec && b->graph_grid != grid) { // the grid is part of the captured launch
-        cudaGraphExecDestroy(b->gexec);
-        b->gexec = nullptr;
-    }
-    if (!b->gexec) {
-        // capture the counter reset and the batched kernel once; they read
-        // the beam table from device memory, so the graph serves any beam set
+    if (b->graph_stale || !b->gexec) {
+        // capture the counter reset and the launches of the current beams;
+        // update the instantiated graph in place when its topology allows
         cudaGraph_t graph = nullptr;
         e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
@@ -265,7 +245,15 @@ hs_status hs_batch_graph_run(hs_batch *b, hs_stream_t stream)
             if (e == cudaSuccess)
                 e = el;
         }
-        if (e == cudaSuccess)
+        if (e == cudaSuccess && b->gexec) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(b->gexec, graph, &info) != cudaSuccess) {
+                cudaGetLastError(); // clear the update failure
+                cudaGraphExecDestroy(b->gexec);
+                b->gexec = nullptr;
+            }
+        }
+        if (e == cudaSuccess && !b->gexec)
             e = cudaGraphInstantiate(&b->gexec, graph, 0);
         if (graph)
             cudaGraphDestroy(graph);
@@ -273,13 +261,22 @@ hs_status hs_batch_graph_run(hs_batch *b, hs_stream_t stream)
             b->gexec = nullptr;
             return cuda_fail(e, "capturing the batch graph");
         }
-        b->graph_grid = grid;
+        b->graph_stale = false;
     }
     e = cudaGraphLaunch(b->gexec, reinterpret_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? HS_OK : cuda_fail(e, "cudaGraphLaunch");
 }
 
 int hs_batch_tiles(const hs_batch *b) { return b ? b->total_tiles : 0; }
+
+int hs_batch_launches(const hs_batch *b)
+{
+    if (!b)
+        return 0;
+    const int k = staged_batch_beams_per_launch(StagedShape{b->nt, b->H, b->tb, b->dtype});
+    const int n = (int)b->beams.size();
+    return k > 0 ? (n + k - 1) / k : 0;
+}
 
 hs_status hs_batch_destroy(hs_batch *b)
 {
@@ -291,9 +288,7 @@ hs_status hs_batch_destroy(hs_batch *b)
     if (b->cap_stream)
         cudaStreamDestroy(b->cap_stream);
     cudaFree(b->d_ta);
-    cudaFree(b->d_beams);
-    cudaFree(b->d_header);
-    cudaFree(b->d_tile_beam);
+    cudaFree(b->d_order);
     delete b;
     return HS_OK;
 }

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -71,28 +72,38 @@ struct StagedLaunch {
 
 cudaError_t launch_staged(const StagedLaunch &a, cudaStream_t s);
 
-// Batched form: many planes (beams) of one shape in one launch.  The beam
-// table lives in device memory (beams: max_beams descriptors of
-// staged_beam_desc_bytes() each; header: {n_beams, total tiles}).
+// Batched form: many planes (beams) of one shape.  Each launch carries the
+// descriptors of up to staged_batch_beams_per_launch() beams in its
+// parameter block; launch_staged_batch clears the beams' counters and issues
+// as many launches as the beam count needs.
+struct StagedBatchBeam {
+    CUtensorMap maps[kMaxStagedH]; // host copies, H descriptors
+    const float *fop32;
+    long long n, ld;
+    hs_cand *rec;
+    uint32_t *counters;
+    uint32_t cap;
+    int tiles;
+};
+
 struct StagedBatch {
     StagedShape sh;
     const float *tmin_host;
     const float *ta;
     float delta, band_abs;
-    const void *beams;
-    const int *header;
-    const int *tile_beam;     // beam of each tile of the batch (device)
-    int max_beams;
-    int grid;                 // CTAs of the launch (they walk the tiles grid-stride)
+    const StagedBatchBeam *beams; // host array
+    int n_beams;
+    const uint32_t *order;        // device: tile order of each beam, concatenated (or null)
+    int grid_per_sm;              // 0: one CTA per tile; k > 0: k resident CTAs per SM
+    int sms;
 };
 
 bool staged_batch_available(const StagedShape &sh);
-size_t staged_beam_desc_bytes();
-void staged_fill_beam_desc(void *dst, const CUtensorMap *maps, int H, const void *fop,
-                           const float *fop32, long long n, long long ld, const hs_cand_buf &cb,
-                           int tile_start);
+int staged_batch_beams_per_launch(const StagedShape &sh);
 
 // Shared host helpers (hs_api.cu)
+// Tile order of a plane of n_tiles tiles: 1 = linear, 2 = octave-interleaved.
+std::vector<uint32_t> tile_order(int n_tiles, int kind);
 CUresult encode_tensor_map(CUtensorMap *map, int dtype, const void *base, long long n_bins,
                            long long ld, int n_templates, int box_w, int box_rows);
 // Prefilter bound of each level group: the smallest threshold of the group

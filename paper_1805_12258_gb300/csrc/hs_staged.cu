@@ -29,6 +29,7 @@
 // non-negative.  For 16-bit planes the bounds are lowered by the storage
 // error too and the slow pass re-evaluates possible hits from the FP32 copy,
 // so candidates match the FP32 path record for record.
+#include <algorithm>
 #include <cstring>
 
 #include "hs_device.cuh"
@@ -173,8 +174,8 @@ __device__ __forceinline__ void issue_tile(const TileTarget &tt, int f0, uint32_
 // Wait for the tile's stage (phase `parity` of `bar`), run the fast pass and
 // the slow pass, append the hits to tt's buffer.  Called by every thread of
 // the CTA; returns false (CTA-uniformly) if the stage did not arrive in time.
-template <int NT, int H, int TB, typename T>
-__device__ __forceinline__ bool sum_tile(const Params<NT, H, T> &p, const TileTarget &tt,
+template <int NT, int H, int TB, typename T, typename P>
+__device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
                                          int f0, const unsigned char *smem, uint32_t bar,
                                          uint32_t parity)
 {
@@ -351,77 +352,91 @@ __global__ void __launch_bounds__(TB, HS_STAGED_MINB * 128 / TB)
     }
 }
 
-// One beam of a batch, in device memory: its descriptors, size, output and
-// first tile in the concatenated tile list of the batch.
-struct alignas(128) BeamDesc {
-    CUtensorMap maps[kMaxStagedH];
-    const void *fop;
+// One beam of a batched launch, carried in the kernel parameters: its
+// descriptors, size, output, and the end of its tiles in the launch's slots.
+template <int H>
+struct BeamParam {
+    CUtensorMap maps[H];
     const float *fop32;
     long long n;
     long long ld;
     hs_cand *rec;
     uint32_t *counters;
     uint32_t cap;
-    int tile_start;
+    int tile_end; // one past the beam's last slot (cumulative over the launch)
 };
 
-// Many beams in one launch: the CTAs walk the concatenated tile list of all
-// beams grid-stride (one tile per CTA when the grid covers the list); the
-// beam of each tile comes from a table, and the beam count, tile count and
-// beam descriptors from device memory, so a captured launch serves any beam
-// set of the same tile count.
+// Largest kernel parameter block the launch accepts.
+constexpr int kParamBytes = 32764;
+
+template <int NT, int H, typename T>
+struct BatchParams {
+    // beams per launch: as many as the parameter block holds (at most 32)
+    static constexpr int K =
+        cmin(32, (kParamBytes - 128) / (int)sizeof(BeamParam<H>));
+    float tmin[n_groups(H)];
+    const float *ta;
+    const uint32_t *order; // per-beam tile order of the whole batch (device) or null
+    float delta;
+    float band_abs;
+    int n_beams;           // beams of this launch
+    int slot_base;         // first slot of this launch in the batch's order table
+    int n_slots;           // tiles of this launch
+    BeamParam<H> beam[K];
+};
+
+// Many beams in one launch.  The descriptors of every beam sit in the
+// parameter block (constant bank), like those of a single-plane launch, so a
+// tile's copies need no proxy fence on descriptors in global memory; the CTAs
+// walk the concatenated tiles of the launch's beams grid-stride (one tile per
+// CTA when the grid covers them) and find each tile's beam by a CTA-uniform
+// scan of the cumulative tile ends.
 template <int NT, int H, int TB, typename T>
 __global__ void __launch_bounds__(TB, HS_STAGED_MINB * 128 / TB)
-    batched_kernel(const __grid_constant__ Params<NT, H, T> p, const BeamDesc *__restrict__ beams,
-                   const int *__restrict__ header /* n_beams, total tiles */,
-                   const int *__restrict__ tile_beam)
+    batched_kernel(const __grid_constant__ BatchParams<NT, H, T> p)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar_storage;
-    __shared__ int cur_beam, cur_tile;
     const uint32_t sbase = smem_addr(smem);
     const uint32_t bar = smem_addr(&bar_storage);
     if (threadIdx.x == 0)
         mbar_init(bar, 1);
     __syncthreads();
-    const int total = __ldg(header + 1);
-    int last_beam = -1; // beam whose descriptors thread 0 last fenced
+    int cur = -1; // beam whose descriptors thread 0 last prefetched
     uint32_t parity = 0;
-    for (int i = (int)blockIdx.x; i < total; i += (int)gridDim.x, parity ^= 1u) {
+    for (int i = (int)blockIdx.x; i < p.n_slots; i += (int)gridDim.x, parity ^= 1u) {
+        int b = 0;
+        while (b + 1 < p.n_beams && i >= p.beam[b].tile_end)
+            ++b;
+        const BeamParam<H> &bp = p.beam[b];
+        const int local = i - (b ? p.beam[b - 1].tile_end : 0);
+        const int tile = p.order ? (int)__ldg(p.order + p.slot_base + i) : local;
+        const TileTarget tt{bp.maps, bp.fop32, bp.n, bp.ld, bp.rec, bp.counters, bp.cap};
         if (threadIdx.x == 0) {
-            const int b = __ldg(tile_beam + i);
-            const BeamDesc &d = beams[b];
-            const int tile = i - d.tile_start;
-            if (b != last_beam) { // descriptors written by the host before the launch
-                static_for<0, H>([&](auto M) {
-                    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
-                                     reinterpret_cast<uint64_t>(&d.maps[M]))
-                                 : "memory");
-                });
-                last_beam = b;
-            }
-            cur_beam = b;
-            cur_tile = tile;
-            const TileTarget tt{d.maps, d.fop32, d.n, d.ld, d.rec, d.counters, d.cap};
+            if (b != cur)
+                static_for<0, H>([&](auto M) { prefetch_tmap(&bp.maps[M]); });
             issue_tile<NT, H, TB, T>(tt, tile * TB, sbase, bar);
         }
-        __syncthreads();
-        const BeamDesc &d = beams[cur_beam];
-        const TileTarget tt{d.maps, d.fop32, d.n, d.ld, d.rec, d.counters, d.cap};
-        if (!sum_tile<NT, H, TB, T>(p, tt, cur_tile * TB, smem, bar, parity))
+        cur = b;
+        if (!sum_tile<NT, H, TB, T>(p, tt, tile * TB, smem, bar, parity))
             break;
         __syncthreads();
     }
 }
 
-// Reset the candidate counters of every beam of a batch.
-__global__ void reset_beam_counters(const BeamDesc *beams, const int *header)
+// Counter pairs to clear before a batched launch, in the parameter block.
+struct CounterList {
+    static constexpr int K = 1024;
+    uint32_t *c[K];
+    int n;
+};
+
+__global__ void reset_counter_list(const __grid_constant__ CounterList l)
 {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < __ldg(header)) {
-        uint32_t *c = beams[b].counters;
-        c[0] = 0u;
-        c[1] = 0u;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < l.n) {
+        l.c[i][0] = 0u;
+        l.c[i][1] = 0u;
     }
 }
 
@@ -471,16 +486,17 @@ template <int NT, int H, int TB, typename T>
 cudaError_t launch_batch_one(const StagedBatch &a, cudaStream_t s)
 {
     using C = Cfg<NT, H, TB, T>;
-    Params<NT, H, T> p;
-    std::memset(&p, 0, sizeof p);
-    for (int g = 0; g < C::G; ++g)
-        p.tmin[g] = a.tmin_host[g];
-    p.ta = a.ta;
-    p.delta = a.delta;
-    p.band_abs = a.band_abs;
-    const BeamDesc *beams = static_cast<const BeamDesc *>(a.beams);
-    reset_beam_counters<<<(a.max_beams + 127) / 128, 128, 0, s>>>(beams, a.header);
-    cudaError_t e = cudaGetLastError();
+    using BP = BatchParams<NT, H, T>;
+    static_assert(sizeof(BP) <= kParamBytes, "parameter block");
+    cudaError_t e = cudaSuccess;
+    for (int b0 = 0; b0 < a.n_beams && e == cudaSuccess; b0 += CounterList::K) {
+        CounterList l;
+        l.n = std::min(CounterList::K, a.n_beams - b0);
+        for (int i = 0; i < l.n; ++i)
+            l.c[i] = a.beams[b0 + i].counters;
+        reset_counter_list<<<(l.n + 127) / 128, 128, 0, s>>>(l);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess)
         return e;
     auto kern = batched_kernel<NT, H, TB, T>;
@@ -489,8 +505,45 @@ cudaError_t launch_batch_one(const StagedBatch &a, cudaStream_t s)
         e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess)
         return e;
-    kern<<<a.grid, TB, C::SMEM, s>>>(p, beams, a.header, a.tile_beam);
-    return cudaGetLastError();
+    BP p; // the parameter block, copied into the launch
+    int slot = 0;
+    for (int b0 = 0; b0 < a.n_beams; b0 += BP::K) {
+        std::memset(&p, 0, sizeof p);
+        for (int g = 0; g < C::G; ++g)
+            p.tmin[g] = a.tmin_host[g];
+        p.ta = a.ta;
+        p.order = a.order;
+        p.delta = a.delta;
+        p.band_abs = a.band_abs;
+        p.n_beams = std::min(BP::K, a.n_beams - b0);
+        p.slot_base = slot;
+        int end = 0;
+        for (int j = 0; j < p.n_beams; ++j) {
+            const StagedBatchBeam &src = a.beams[b0 + j];
+            BeamParam<H> &d = p.beam[j];
+            std::memcpy(d.maps, src.maps, sizeof(CUtensorMap) * H);
+            d.fop32 = src.fop32;
+            d.n = src.n;
+            d.ld = src.ld;
+            d.rec = src.rec;
+            d.counters = src.counters;
+            d.cap = src.cap;
+            end += src.tiles;
+            d.tile_end = end;
+        }
+        p.n_slots = end;
+        slot += end;
+        if (end == 0)
+            continue;
+        int grid = end;
+        if (a.grid_per_sm > 0 && a.sms * a.grid_per_sm < grid)
+            grid = a.sms * a.grid_per_sm;
+        kern<<<grid, TB, C::SMEM, s>>>(p);
+        e = cudaGetLastError();
+        if (e != cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
 }
 
 template <int NT, int H, int TB, typename T>
@@ -553,24 +606,14 @@ void staged_box(const StagedShape &sh, int m, int *width, int *rows)
 #undef X
 }
 
-size_t staged_beam_desc_bytes() { return sizeof(BeamDesc); }
-
-void staged_fill_beam_desc(void *dst, const CUtensorMap *maps, int H, const void *fop,
-                           const float *fop32, long long n, long long ld, const hs_cand_buf &cb,
-                           int tile_start)
+int staged_batch_beams_per_launch(const StagedShape &sh)
 {
-    BeamDesc d;
-    std::memset(&d, 0, sizeof d);
-    std::memcpy(d.maps, maps, sizeof(CUtensorMap) * H);
-    d.fop = fop;
-    d.fop32 = fop32;
-    d.n = n;
-    d.ld = ld;
-    d.rec = cb.records;
-    d.counters = cb.count;
-    d.cap = cb.capacity;
-    d.tile_start = tile_start;
-    std::memcpy(dst, &d, sizeof d);
+#define X(NT_, H_, TB_, T_, DT_)                                                              \
+    if (sh.nt == NT_ && sh.H == H_ && sh.tb == TB_ && sh.dtype == DT_)                       \
+        return BatchParams<NT_, H_, T_>::K;
+    HS_BATCH_SHAPES(X)
+#undef X
+    return 0;
 }
 
 bool staged_batch_available(const StagedShape &sh)

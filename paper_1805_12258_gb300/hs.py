@@ -105,6 +105,8 @@ def lib():
     L.hs_batch_destroy.argtypes = [vp]
     L.hs_batch_tiles.argtypes = [vp]
     L.hs_batch_tiles.restype = i32
+    L.hs_batch_launches.argtypes = [vp]
+    L.hs_batch_launches.restype = i32
     L.hs_batch_last_error.argtypes = []
     L.hs_batch_last_error.restype = ctypes.c_char_p
     for name in ("hs_batch_create", "hs_batch_set_beams", "hs_batch_run", "hs_batch_graph_run",
@@ -341,16 +343,16 @@ def _batch_check(status, what):
 
 
 class Batch:
-    """An hs_batch: many planes of one shape (each with its own bin count)
-    summed by one launch over all their tiles; graph_run replays a captured
-    CUDA graph of that launch."""
+    """An hs_batch: many planes of one shape (each with its own bin count and
+    row pitch) summed by a few launches, each carrying up to K beams'
+    descriptors; graph_run replays a captured CUDA graph of those launches."""
 
     def __init__(self, n_templates, H, thresholds, *, dtype="f32", grid_per_sm=0,
-                 max_beams=64):
+                 max_beams=64, order=0):
         ta = np.ascontiguousarray(thresholds, dtype=np.float32)
         if ta.shape != (H, n_templates):
             raise ValueError(f"thresholds must have shape {(H, n_templates)}, got {ta.shape}")
-        opt = hs_options(DTYPES[dtype], 0, 0, 0, 0, 0, int(grid_per_sm), 0)
+        opt = hs_options(DTYPES[dtype], 0, 0, 0, 0, int(order), int(grid_per_sm), 0)
         out = ctypes.c_void_p()
         _batch_check(lib().hs_batch_create(ctypes.byref(out), n_templates, H, ta.ctypes.data,
                                            ctypes.byref(opt), int(max_beams)), "hs_batch_create")
@@ -374,6 +376,11 @@ class Batch:
     @property
     def tiles(self):
         return lib().hs_batch_tiles(self.handle)
+
+    @property
+    def launches(self):
+        """Kernel launches one run issues to sum the tiles (reset excluded)."""
+        return lib().hs_batch_launches(self.handle)
 
     def run(self, stream=None):
         _batch_check(lib().hs_batch_run(self.handle, _stream_handle(stream)), "hs_batch_run")

@@ -64,6 +64,32 @@ def test_batch_matches_per_plane_runs_and_graph_replay(nt, H, gps):
                 assert np.array_equal(got, _plan_records(plane, H, ta))
 
 
+@pytest.mark.parametrize("nt,H,order", [(85, 16, 0), (21, 8, 0), (85, 16, 1)])
+def test_batch_spanning_several_launches(nt, H, order):
+    # more beams than one launch's parameter block holds: the run splits them
+    # over launches; graph replays, and re-captures after the beam set
+    # changes, give the same records
+    rng = np.random.default_rng(7 + nt + order)
+    ta = synth.thresholds(1e-3, H, nt)
+    sizes = [int(x) for x in rng.integers(100, 6000, size=37)]
+    items = []
+    for i, n in enumerate(sizes):
+        plane, dev = _beam(nt, n, seed=500 + i)
+        items.append((plane, dev, n, hs.CandBuffer(1 << 14)))
+    refs = [_plan_records(plane, H, ta) for plane, _, _, _ in items]
+    with hs.Batch(nt, H, ta, max_beams=64, order=order) as batch:
+        for subset in (range(37), range(5, 25), range(37)):
+            sel = list(subset)
+            batch.set_beams([(items[i][1], items[i][2], items[i][3]) for i in sel])
+            assert batch.launches >= (2 if len(sel) > 30 else 1)
+            for rep in range(2):
+                batch.graph_run()
+                for i in sel:
+                    got, cnt, st = items[i][3].fetch()
+                    assert st == hs.HS_OK
+                    assert np.array_equal(got, refs[i]), (i, rep)
+
+
 def test_batch_beam_against_oracle():
     nt, H, n = 85, 16, 30011
     ta = synth.thresholds(1e-4, H, nt)
