@@ -46,7 +46,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ska", choices=["ska", "small", "batch"])
+    ap.add_argument("--workload", default="ska", choices=["ska", "small", "batch", "serve"])
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="serve workload: length of the Poisson arrival phase")
+    ap.add_argument("--serve-rate", type=float, default=1000.0, help="arrivals per second")
+    ap.add_argument("--slots", type=int, default=16, help="serve workload: resident slots")
     ap.add_argument("--grid-per-sm", type=int, default=0)
     ap.add_argument("--beams", type=int, default=64)
     ap.add_argument("--beam-log2", default="18,22",
@@ -481,12 +485,136 @@ def run_batch(args):
     }), flush=True)
 
 
+def run_serve(args):
+    """The serving engine under Poisson arrivals (seed 4) of beams with
+    85 templates x n_bins log-uniform in [2^18, 2^22], H = 16, FP32 or BF16
+    (50/50), 0-10 injected signals each; then a closed-loop phase that keeps
+    the queue full to measure the engine's capacity."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    from paper_1805_12258_gb300 import build as hsbuild
+    from paper_1805_12258_gb300 import hs, synth
+
+    torch.cuda.set_device(0)
+    hsbuild.build()
+    nt, H = 85, 16
+    ta = synth.thresholds(1e-8, H, nt)
+    rng = np.random.Generator(np.random.Philox(4))
+    lo, hi = (float(x) for x in args.beam_log2.split(","))
+
+    def draw(k):
+        n = np.rint(2.0 ** rng.uniform(lo, hi, size=k)).astype(np.int64)
+        dt = np.where(rng.random(k) < 0.5, "bf16", "f32")
+        sig = rng.integers(0, 11, size=k)
+        return n, dt, sig
+
+    n_max = int(round(2.0 ** hi))
+    with hs.Server(nt, H, ta, n_slots=args.slots, slot_bins=n_max, cand_capacity=4096,
+                   queue_limit=1 << 16) as srv:
+        # warm-up: every path once (allocations, first launches)
+        wn, wd, ws = draw(2 * args.slots)
+        warm = [srv.submit(10**6 + i, int(wn[i]), str(wd[i]), int(ws[i])) for i in range(len(wn))]
+        for t in warm:
+            srv.wait(t)
+
+        def phase(n_bins, dts, sigs, arrivals, seed0):
+            """Submit at the arrival times (None: as fast as admission
+            allows); a second thread collects results in submit order."""
+            results, tickets, rejected = [], [], [0]
+            done = threading.Event()
+
+            def collect():
+                i = 0
+                while True:
+                    if i < len(tickets):
+                        out = srv.wait(tickets[i])
+                        results.append(out[0])
+                        i += 1
+                    elif done.is_set():
+                        return
+                    else:
+                        time.sleep(0.0002)
+
+            th = threading.Thread(target=collect)
+            th.start()
+            t0 = time.perf_counter()
+            for i in range(len(n_bins)):
+                if arrivals is not None:
+                    dt = t0 + arrivals[i] - time.perf_counter()
+                    if dt > 0:
+                        time.sleep(dt)
+                while True:
+                    t = srv.submit(seed0 + i, int(n_bins[i]), str(dts[i]), int(sigs[i]))
+                    if t is not None:
+                        tickets.append(t)
+                        break
+                    if arrivals is not None:
+                        rejected[0] += 1
+                        break
+                    time.sleep(0.0002)  # closed loop: wait for room
+            done.set()
+            th.join()
+            return results, rejected[0]
+
+        # open loop: Poisson arrivals
+        k = int(args.serve_rate * args.serve_seconds * 1.2) + 16
+        gaps = rng.exponential(1.0 / args.serve_rate, size=k)
+        arr = np.cumsum(gaps)
+        k = int(np.searchsorted(arr, args.serve_seconds))
+        n_bins, dts, sigs = draw(k)
+        clocks = ClockSampler(0)
+        clocks.start()
+        res_open, rej = phase(n_bins, dts, sigs, arr[:k], 2 * 10**6)
+        # closed loop: queue kept full for capacity
+        kc = max(64, int(args.serve_rate * 3))
+        cn, cd, cs = draw(kc)
+        res_closed, _ = phase(cn, cd, cs, None, 3 * 10**6)
+        clk = clocks.stop()
+        st = srv.stats()
+
+    def summary(results, n_bins):
+        lat = np.array([(r["t_done_ns"] - r["t_submit_ns"]) / 1e6 for r in results])
+        svc = np.array([(r["t_done_ns"] - r["t_admit_ns"]) / 1e6 for r in results])
+        span = (max(r["t_done_ns"] for r in results) - min(r["t_submit_ns"] for r in results)) / 1e9
+        pts = nt * int(np.sum(n_bins[:len(results)]))
+        bad = sum(r["status"] != hs.HS_OK for r in results)
+        return {"requests": len(results), "failed": bad,
+                "latency_ms": {"p50": float(np.percentile(lat, 50)),
+                               "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
+                "service_ms": {"p50": float(np.percentile(svc, 50)),
+                               "p99": float(np.percentile(svc, 99))},
+                "points_per_s": pts / span, "seconds": span,
+                "mean_group": float(np.mean([r["group_size"] for r in results]))}
+
+    so, sc = summary(res_open, n_bins), summary(res_closed, cn)
+    print(json.dumps({
+        "metric": "FOP points harmonic-summed/s served (capacity, queue kept full)",
+        "value": sc["points_per_s"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16",
+        "data": "synthetic (planes generated on the device per request)",
+        "config": {"workload": f"serving: Poisson {args.serve_rate:g} beams/s for "
+                               f"{args.serve_seconds:g} s, 85 templates x n_bins log-uniform in "
+                               f"[2^{lo:g}, 2^{hi:g}], H=16, FP32/BF16 50/50, 0-10 signals",
+                   "slots": args.slots, "l2": "inputs larger than L2"},
+        "open_loop": dict(so, rejected=rej, offered_per_s=args.serve_rate),
+        "closed_loop": sc,
+        "latency": "steady clock from hs_server_submit to the candidates in host memory "
+                   "(service: from admission into a slot)",
+        "stats": st, "clocks": clk, "e2e": None, "cpu_baseline": None,
+    }), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

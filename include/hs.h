@@ -57,7 +57,8 @@ typedef enum {
     HS_ERR_OOM = 3,         /* device or host allocation failed */
     HS_ERR_OVERFLOW = 4,    /* more candidates than the buffer holds */
     HS_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
-    HS_ERR_UNSUPPORTED = 6  /* valid request this build does not implement */
+    HS_ERR_UNSUPPORTED = 6, /* valid request this build does not implement */
+    HS_ERR_BUSY = 7         /* serving engine: queue full, or result not ready in time */
 } hs_status;
 
 typedef enum { HS_F32 = 0, HS_BF16 = 1, HS_F16 = 2 } hs_dtype;
@@ -212,6 +213,102 @@ HS_API int hs_batch_launches(const hs_batch *b);
 /* Destroy a batch (NULL is accepted); synchronises the device first. */
 HS_API hs_status hs_batch_destroy(hs_batch *b);
 HS_API const char *hs_batch_last_error(void);
+
+/* ---- Serving form: a long-lived engine over resident plane slots ----------
+ * The paper's pipeline feeds harmonic summing one plane per DM trial, as the
+ * upstream Fourier-domain convolution produces them (Section II, Fig. 1), with
+ * thousands of planes per observation (Section VI-C).  The engine keeps
+ * n_slots plane slots resident in device memory (memory admission: a request
+ * runs only when a slot is free; at most queue_limit wait, further submits
+ * answer HS_ERR_BUSY), produces each admitted request's plane on the device
+ * into its slot with hs_synth_fop (standing in for the upstream stage), and
+ * sums every group of admitted requests with the batched kernels (FP32 and
+ * BF16 requests mixed; BF16 planes keep an FP32 copy for rechecks, so their
+ * candidates equal the FP32 path's).  A dispatcher thread admits and launches
+ * groups while earlier groups run (continuous batching); a completion thread
+ * copies each request's candidates to host memory and frees its slot.  One
+ * request's candidates do not depend on what it ran with. */
+typedef struct {
+    int n_templates;          /* rows of every plane (odd; 85 or 21 compiled) */
+    int H;                    /* levels (16 for 85 rows, 8 for 21) */
+    const float *thresholds;  /* host TA[H][n_templates], copied */
+    int n_slots;              /* resident slots (1..1024), reserved at create */
+    int64_t slot_bins;        /* largest n_bins of a request */
+    uint32_t cand_capacity;   /* records kept per request (1..2^20) */
+    int queue_limit;          /* requests waiting for a slot (>= 0) */
+    int max_group;            /* requests admitted into one group (0 = n_slots) */
+} hs_server_config;
+
+typedef struct {
+    uint64_t seed;            /* generator seed of the plane (noise and signals) */
+    int64_t n_bins;           /* 1..slot_bins */
+    int dtype;                /* HS_F32 or HS_BF16 */
+    int n_signals;            /* injected signals, 0..16 */
+} hs_request;
+
+typedef struct {
+    uint64_t ticket;
+    hs_status status;         /* HS_OK, HS_ERR_OVERFLOW, HS_ERR_TIMEOUT or HS_ERR_CUDA */
+    uint32_t n_cands;         /* true hit count; min(n_cands, cand_capacity) records kept */
+    int32_t group;            /* admission group that ran the request */
+    int32_t group_size;       /* requests in that group */
+    int32_t slot;
+    int64_t t_submit_ns;      /* steady clock: submit, admission, candidates on host */
+    int64_t t_admit_ns;
+    int64_t t_done_ns;
+} hs_result;
+
+typedef struct {
+    uint64_t submitted, rejected, completed, groups;
+    uint64_t points;          /* n_templates x n_bins summed over completed requests */
+    int32_t queued, in_flight, free_slots, peak_queue;
+} hs_server_stats;
+
+typedef struct hs_server hs_server;
+
+/* Create an engine on the current device: reserves n_slots slots of
+ * n_templates x round_up(slot_bins, 8) elements at 6 bytes each (FP32 plane
+ * or FP32 copy + BF16 plane) plus the candidate buffers, and starts the
+ * dispatcher and completion threads.
+ * Errors: HS_ERR_INVALID, HS_ERR_UNSUPPORTED (no batched kernel for the
+ * shape), HS_ERR_OOM, HS_ERR_CUDA. */
+HS_API hs_status hs_server_create(hs_server **out, const hs_server_config *cfg);
+
+/* Queue a request; *ticket identifies it.  HS_ERR_BUSY when queue_limit
+ * requests already wait for a slot (nothing is queued), HS_ERR_INVALID for a
+ * bad request. */
+HS_API hs_status hs_server_submit(hs_server *s, const hs_request *r, uint64_t *ticket);
+
+/* Wait up to timeout_ms (< 0: forever) for a request to finish; on success
+ * fills *res, copies up to `capacity` records to host memory `records` (may
+ * be NULL) and forgets the request.  Returns HS_ERR_BUSY if it did not finish
+ * in time, HS_ERR_INVALID for an unknown ticket; otherwise HS_OK (the
+ * request's own outcome is res->status). */
+HS_API hs_status hs_server_wait(hs_server *s, uint64_t ticket, int timeout_ms, hs_result *res,
+                                hs_cand *records, uint32_t capacity);
+
+/* Wait up to timeout_ms (< 0: forever) until nothing is queued or running. */
+HS_API hs_status hs_server_drain(hs_server *s, int timeout_ms);
+
+HS_API hs_status hs_server_stats_get(hs_server *s, hs_server_stats *st);
+
+/* Stop the threads (finishing admitted work) and free everything; NULL ok. */
+HS_API hs_status hs_server_destroy(hs_server *s);
+HS_API const char *hs_server_last_error(void);
+
+/* The plane generator of the serving engine, standing in for the upstream
+ * stage: writes iid Exponential(mean 1) noise -- Philox4x32-10 (Salmon et
+ * al., SC'11) keyed by seed, counter (bin / 4, row) -- into the
+ * n_templates x n_bins plane with row pitch ld (>= n_bins, multiple of 8;
+ * pad bins are zeroed), then adds n_signals harmonic signals (amplitude
+ * U[3, 8) at (h z0, h f0) for h = 1..16 inside the plane; z0 in [-2, 2], f0
+ * drawn from the seed).  dtype HS_F32: fop is the FP32 plane, fop32 unused.
+ * dtype HS_BF16: fop receives the BF16 plane (round to nearest even) and
+ * fop32 the FP32 values.  Pointers 16-byte aligned.
+ * Errors: HS_ERR_INVALID, HS_ERR_CUDA. */
+HS_API hs_status hs_synth_fop(void *fop, float *fop32, int dtype, int n_templates,
+                              int64_t n_bins, int64_t ld, uint64_t seed, int n_signals,
+                              hs_stream_t stream);
 
 /* Harmonic summing with no device allocation.  The paper has no counterpart:
  * this entry point is for callers that may not allocate device memory, such

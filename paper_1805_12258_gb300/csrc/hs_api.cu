@@ -275,6 +275,7 @@ const char *hs_status_str(hs_status s)
     case HS_ERR_OVERFLOW: return "candidate buffer overflow";
     case HS_ERR_TIMEOUT: return "device wait timed out";
     case HS_ERR_UNSUPPORTED: return "unsupported";
+    case HS_ERR_BUSY: return "busy (queue full or not finished)";
     }
     return "unknown status";
 }

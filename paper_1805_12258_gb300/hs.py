@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libhs.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "hs.h")
 
 HS_OK, HS_ERR_INVALID, HS_ERR_CUDA, HS_ERR_OOM, HS_ERR_OVERFLOW, HS_ERR_TIMEOUT, \
-    HS_ERR_UNSUPPORTED = range(7)
+    HS_ERR_UNSUPPORTED, HS_ERR_BUSY = range(8)
 HS_F32, HS_BF16, HS_F16 = 0, 1, 2
 HS_INDEX_STRETCH, HS_INDEX_HFRAC = 0, 1
 HS_ZROUND_SYMMETRIC, HS_ZROUND_FLOOR = 0, 1
@@ -64,6 +64,34 @@ class hs_cand_buf(ctypes.Structure):
 class hs_beam(ctypes.Structure):
     _fields_ = [("fop", ctypes.c_void_p), ("fop32", ctypes.c_void_p), ("n_bins", ctypes.c_int64),
                 ("ld", ctypes.c_int64), ("cands", hs_cand_buf)]
+
+
+class hs_server_config(ctypes.Structure):
+    _fields_ = [("n_templates", ctypes.c_int), ("H", ctypes.c_int),
+                ("thresholds", ctypes.c_void_p), ("n_slots", ctypes.c_int),
+                ("slot_bins", ctypes.c_int64), ("cand_capacity", ctypes.c_uint32),
+                ("queue_limit", ctypes.c_int), ("max_group", ctypes.c_int)]
+
+
+class hs_request(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("n_bins", ctypes.c_int64), ("dtype", ctypes.c_int),
+                ("n_signals", ctypes.c_int)]
+
+
+class hs_result(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int),
+                ("n_cands", ctypes.c_uint32), ("group", ctypes.c_int32),
+                ("group_size", ctypes.c_int32), ("slot", ctypes.c_int32),
+                ("t_submit_ns", ctypes.c_int64), ("t_admit_ns", ctypes.c_int64),
+                ("t_done_ns", ctypes.c_int64)]
+
+
+class hs_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
+                ("completed", ctypes.c_uint64), ("groups", ctypes.c_uint64),
+                ("points", ctypes.c_uint64), ("queued", ctypes.c_int32),
+                ("in_flight", ctypes.c_int32), ("free_slots", ctypes.c_int32),
+                ("peak_queue", ctypes.c_int32)]
 
 
 _lib = None
@@ -111,6 +139,18 @@ def lib():
     L.hs_batch_last_error.restype = ctypes.c_char_p
     for name in ("hs_batch_create", "hs_batch_set_beams", "hs_batch_run", "hs_batch_graph_run",
                  "hs_batch_destroy"):
+        getattr(L, name).restype = i32
+    L.hs_server_create.argtypes = [P(vp), P(hs_server_config)]
+    L.hs_server_submit.argtypes = [vp, P(hs_request), P(ctypes.c_uint64)]
+    L.hs_server_wait.argtypes = [vp, ctypes.c_uint64, i32, P(hs_result), vp, u32]
+    L.hs_server_drain.argtypes = [vp, i32]
+    L.hs_server_stats_get.argtypes = [vp, P(hs_server_stats)]
+    L.hs_server_destroy.argtypes = [vp]
+    L.hs_server_last_error.argtypes = []
+    L.hs_server_last_error.restype = ctypes.c_char_p
+    L.hs_synth_fop.argtypes = [vp, vp, i32, i32, i64, i64, ctypes.c_uint64, i32, vp]
+    for name in ("hs_server_create", "hs_server_submit", "hs_server_wait", "hs_server_drain",
+                 "hs_server_stats_get", "hs_server_destroy", "hs_synth_fop"):
         getattr(L, name).restype = i32
     L.hs_run_noalloc.argtypes = [i32, i64, i32, vp, vp, vp, P(hs_cand_buf)]
     L.hs_run_noalloc.restype = i32
@@ -392,6 +432,89 @@ class Batch:
     def close(self):
         if getattr(self, "handle", None):
             lib().hs_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+# ---- serving form ----------------------------------------------------------------
+
+def hs_synth_fop(fop, fop32, dtype, n_templates, n_bins, ld, seed, n_signals, stream=None):
+    """Device plane generator (Exponential(1) noise by Philox4x32-10 plus
+    harmonic signals) into fop (and fop32 for BF16)."""
+    st = lib().hs_synth_fop(_ptr(fop), _ptr(fop32), DTYPES[dtype] if isinstance(dtype, str)
+                            else int(dtype), int(n_templates), int(n_bins), int(ld), int(seed),
+                            int(n_signals), _stream_handle(stream))
+    if st != HS_OK:
+        raise HsError(st, f"hs_synth_fop: {lib().hs_server_last_error().decode()}")
+
+
+class Server:
+    """An hs_server: resident plane slots, a dispatcher that admits queued
+    requests into free slots and sums each admitted group with the batched
+    kernels, and a completion thread that returns candidates to the host."""
+
+    def __init__(self, n_templates, H, thresholds, *, n_slots=16, slot_bins=1 << 22,
+                 cand_capacity=4096, queue_limit=1024, max_group=0):
+        ta = np.ascontiguousarray(thresholds, dtype=np.float32)
+        if ta.shape != (H, n_templates):
+            raise ValueError(f"thresholds must have shape {(H, n_templates)}, got {ta.shape}")
+        cfg = hs_server_config(n_templates, H, ta.ctypes.data, int(n_slots), int(slot_bins),
+                               int(cand_capacity), int(queue_limit), int(max_group))
+        out = ctypes.c_void_p()
+        st = lib().hs_server_create(ctypes.byref(out), ctypes.byref(cfg))
+        if st != HS_OK:
+            raise HsError(st, f"hs_server_create: {lib().hs_server_last_error().decode()}")
+        self.handle = out.value
+        self.n_templates, self.H, self.cand_capacity = n_templates, H, int(cand_capacity)
+
+    def submit(self, seed, n_bins, dtype="f32", n_signals=0):
+        """Queue a request; returns its ticket, or None when the queue is full."""
+        req = hs_request(int(seed), int(n_bins), DTYPES[dtype], int(n_signals))
+        t = ctypes.c_uint64()
+        st = lib().hs_server_submit(self.handle, ctypes.byref(req), ctypes.byref(t))
+        if st == HS_ERR_BUSY:
+            return None
+        if st != HS_OK:
+            raise HsError(st, f"hs_server_submit: {lib().hs_server_last_error().decode()}")
+        return t.value
+
+    def wait(self, ticket, timeout_ms=-1):
+        """(result dict, records sorted by (k, z, bin)) or None on timeout."""
+        res = hs_result()
+        recs = np.zeros(self.cand_capacity, dtype=CAND_DTYPE)
+        st = lib().hs_server_wait(self.handle, int(ticket), int(timeout_ms), ctypes.byref(res),
+                                  recs.ctypes.data, self.cand_capacity)
+        if st == HS_ERR_BUSY:
+            return None
+        if st != HS_OK:
+            raise HsError(st, f"hs_server_wait: {lib().hs_server_last_error().decode()}")
+        d = {name: getattr(res, name) for name, _ in hs_result._fields_}
+        kept = min(res.n_cands, self.cand_capacity) if res.status in (HS_OK, HS_ERR_OVERFLOW) \
+            else 0
+        return d, sort_records(recs[:kept])
+
+    def drain(self, timeout_ms=-1):
+        return lib().hs_server_drain(self.handle, int(timeout_ms)) == HS_OK
+
+    def stats(self):
+        st = hs_server_stats()
+        lib().hs_server_stats_get(self.handle, ctypes.byref(st))
+        return {name: getattr(st, name) for name, _ in hs_server_stats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().hs_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

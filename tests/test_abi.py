@@ -2,6 +2,7 @@
 every function include/hs.h declares, and its host-side validation and
 helpers behave (no compute call needs a GPU here)."""
 import ctypes
+import os
 
 import numpy as np
 import pytest
@@ -90,3 +91,35 @@ def test_pack_paper(L):
     rec["k"], rec["bin"] = 1, 1 << 21
     with pytest.raises(hs.HsError):
         hs.hs_pack_paper(rec, 85)
+
+
+def test_c_struct_layouts_match_the_binding(tmp_path):
+    """The header's structs as a C compiler lays them out equal the ctypes
+    mirrors the binding passes across the boundary."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    names = ["hs_options", "hs_cand", "hs_cand_buf", "hs_beam", "hs_server_config",
+             "hs_request", "hs_result", "hs_server_stats"]
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include "hs.h"\nint main(void){\n' +
+                   "".join(f'printf("%zu\\n", sizeof({n}));\n' for n in names) +
+                   "return 0;}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.dirname(hs.HEADER), str(src), "-o", str(exe)], check=True)
+    sizes = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True,
+                                            text=True).stdout.split()]
+    assert sizes == [ctypes.sizeof(getattr(hs, n)) for n in names]
+
+
+def test_server_and_generator_validate_before_touching_the_device(L):
+    out = ctypes.c_void_p()
+    assert L.hs_server_create(ctypes.byref(out), None) == hs.HS_ERR_INVALID
+    cfg = hs.hs_server_config(85, 16, None, 4, 1000, 16, 0, 0)
+    assert L.hs_server_create(ctypes.byref(out), ctypes.byref(cfg)) == hs.HS_ERR_INVALID
+    assert L.hs_synth_fop(None, None, 0, 85, 100, 104, 1, 0, None) == hs.HS_ERR_INVALID
+    assert L.hs_server_submit(None, None, None) == hs.HS_ERR_INVALID
+    assert L.hs_server_destroy(None) == hs.HS_OK
+    assert "busy" in hs.hs_status_str(hs.HS_ERR_BUSY)
