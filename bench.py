@@ -419,7 +419,7 @@ def run_batch(args):
         gps = best["grid_per_sm"]
         tuned = table
     stream = torch.cuda.current_stream()
-    with hs.Batch(nt, H, ta, grid_per_sm=gps, max_beams=len(beams)) as batch:
+    with hs.Batch(nt, H, ta, grid_per_sm=gps, max_beams=len(beams), order=args.order) as batch:
         batch.set_beams(beams)
         for _ in range(max(3, args.warmup)):
             batch.graph_run(stream)
@@ -469,6 +469,7 @@ def run_batch(args):
                                f"log-uniform in [2^{lo:g}, 2^{hi:g}], H=16 fp32",
                    "beams": len(beams), "bins_total": sum(sizes), "tiles": tiles,
                    "launches_per_step": 1 + launches,
+                   "tile_order": "linear" if args.order == 1 else "octave-interleaved",
                    "grid_per_sm": gps, "graph": True, "candidates": n_cand,
                    "l2": "inputs larger than L2, no flush"},
         "sequential_hs_run_ms": t_seq, "batch_speedup_vs_sequential": t_seq / ms,
@@ -580,7 +581,8 @@ def run_serve(args):
         svc = np.array([(r["t_done_ns"] - r["t_admit_ns"]) / 1e6 for r in results])
         span = (max(r["t_done_ns"] for r in results) - min(r["t_submit_ns"] for r in results)) / 1e9
         pts = nt * int(np.sum(n_bins[:len(results)]))
-        bad = sum(r["status"] != hs.HS_OK for r in results)
+        bad = {"overflow": sum(r["status"] == hs.HS_ERR_OVERFLOW for r in results),
+               "other": sum(r["status"] not in (hs.HS_OK, hs.HS_ERR_OVERFLOW) for r in results)}
         return {"requests": len(results), "failed": bad,
                 "latency_ms": {"p50": float(np.percentile(lat, 50)),
                                "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
@@ -590,6 +592,21 @@ def run_serve(args):
                 "mean_group": float(np.mean([r["group_size"] for r in results]))}
 
     so, sc = summary(res_open, n_bins), summary(res_closed, cn)
+    # the plane generator alone (the upstream stand-in each request pays for)
+    gen = {}
+    ld = (n_max + 7) // 8 * 8
+    f32 = torch.empty((nt, ld), dtype=torch.float32, device="cuda")
+    b16 = torch.empty((nt, ld), dtype=torch.bfloat16, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for name in ("f32", "bf16"):
+        for rep in range(4):
+            e0.record()
+            hs.hs_synth_fop(f32 if name == "f32" else b16, None if name == "f32" else f32, name,
+                            nt, n_max, ld, 99 + rep, 10)
+            e1.record()
+            torch.cuda.synchronize()
+        gen[name] = e0.elapsed_time(e1)
+    del f32, b16
     print(json.dumps({
         "metric": "FOP points harmonic-summed/s served (capacity, queue kept full)",
         "value": sc["points_per_s"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
@@ -603,6 +620,7 @@ def run_serve(args):
         "closed_loop": sc,
         "latency": "steady clock from hs_server_submit to the candidates in host memory "
                    "(service: from admission into a slot)",
+        "generator_ms_per_2^22_plane": gen,
         "stats": st, "clocks": clk, "e2e": None, "cpu_baseline": None,
     }), flush=True)
 

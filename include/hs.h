@@ -261,6 +261,7 @@ typedef struct {
 typedef struct {
     uint64_t submitted, rejected, completed, groups;
     uint64_t points;          /* n_templates x n_bins summed over completed requests */
+    uint64_t dispatch_ns;     /* host time the dispatcher spent enqueuing groups */
     int32_t queued, in_flight, free_slots, peak_queue;
 } hs_server_stats;
 
@@ -268,8 +269,10 @@ typedef struct hs_server hs_server;
 
 /* Create an engine on the current device: reserves n_slots slots of
  * n_templates x round_up(slot_bins, 8) elements at 6 bytes each (FP32 plane
- * or FP32 copy + BF16 plane) plus the candidate buffers, and starts the
- * dispatcher and completion threads.
+ * or FP32 copy + BF16 plane; every request keeps the slot's row pitch, so
+ * the slots' TMA descriptors are encoded once here) plus the candidate
+ * buffers, and starts the dispatcher and completion threads.  Groups
+ * alternate between two streams.
  * Errors: HS_ERR_INVALID, HS_ERR_UNSUPPORTED (no batched kernel for the
  * shape), HS_ERR_OOM, HS_ERR_CUDA. */
 HS_API hs_status hs_server_create(hs_server **out, const hs_server_config *cfg);

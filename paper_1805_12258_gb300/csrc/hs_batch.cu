@@ -28,6 +28,7 @@ struct hs_batch {
     uint32_t *d_order = nullptr; // tile order of each beam, concatenated
     long long order_cap = 0;
     std::vector<uint32_t> h_order;
+    std::vector<uint32_t> order_full; // order of the largest beam seen (a filter gives smaller ones)
     int grid_per_sm = 0;         // 0: one CTA per tile
     int sms = 0;
     std::mutex mu;
@@ -137,6 +138,69 @@ hs_status hs_batch_create(hs_batch **out, int n_templates, int H, const float *t
     return HS_OK;
 }
 
+} // extern "C"
+
+hs_status hs::batch_set_prepared(hs_batch *b, const StagedBatchBeam *beams, int n_beams,
+                                 cudaStream_t s)
+{
+    if (n_beams < 0 || n_beams > b->max_beams)
+        return fail(HS_ERR_INVALID, "n_beams must be in [0, max_beams]");
+    std::vector<StagedBatchBeam> nb(beams, beams + n_beams);
+    long long total = 0;
+    for (const StagedBatchBeam &d : nb)
+        total += d.tiles;
+    if (total > 0x7fffffffLL)
+        return fail(HS_ERR_INVALID, "batch has more than 2^31 tiles");
+    std::lock_guard<std::mutex> lk(b->mu);
+    cudaError_t e = cudaSuccess;
+    if (b->order != 1) {
+        // the octave order of t < k tiles is the octave order of more tiles
+        // with the entries >= k dropped (the sort key depends on t alone)
+        int most = 0;
+        for (const StagedBatchBeam &d : nb)
+            most = std::max(most, d.tiles);
+        if ((int)b->order_full.size() < most)
+            b->order_full = tile_order(most, b->order);
+        b->h_order.resize((size_t)total);
+        size_t at = 0;
+        for (const StagedBatchBeam &d : nb) {
+            if ((int)b->order_full.size() == d.tiles) {
+                std::copy(b->order_full.begin(), b->order_full.end(), b->h_order.begin() + (long)at);
+                at += (size_t)d.tiles;
+            } else {
+                for (uint32_t t : b->order_full)
+                    if ((int)t < d.tiles)
+                        b->h_order[at++] = t;
+            }
+        }
+        if (total > b->order_cap) {
+            // the old table may still be read by queued runs: wait for them
+            e = cudaStreamSynchronize(s);
+            if (e == cudaSuccess) {
+                cudaFree(b->d_order);
+                b->d_order = nullptr;
+                b->order_cap = 0;
+                e = cudaMalloc(&b->d_order, sizeof(uint32_t) * (size_t)total);
+            }
+            if (e != cudaSuccess)
+                return cuda_fail(e, "allocating the tile order table");
+            b->order_cap = total;
+        }
+        // pageable source: the copy completes its host-side read before return
+        if (total > 0)
+            e = cudaMemcpyAsync(b->d_order, b->h_order.data(), sizeof(uint32_t) * (size_t)total,
+                                cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "uploading the tile order");
+    }
+    b->beams.swap(nb);
+    b->total_tiles = (int)total;
+    b->graph_stale = true;
+    return HS_OK;
+}
+
+extern "C" {
+
 hs_status hs_batch_set_beams(hs_batch *b, const hs_beam *beams, int n_beams, hs_stream_t stream)
 {
     if (!b || (!beams && n_beams > 0))
@@ -182,41 +246,7 @@ hs_status hs_batch_set_beams(hs_batch *b, const hs_beam *beams, int n_beams, hs_
         if (total > 0x7fffffffLL)
             return fail(HS_ERR_INVALID, "batch has more than 2^31 tiles");
     }
-    std::lock_guard<std::mutex> lk(b->mu);
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaSuccess;
-    if (b->order != 1) {
-        b->h_order.resize((size_t)total);
-        size_t at = 0;
-        for (const StagedBatchBeam &d : nb) {
-            const std::vector<uint32_t> o = tile_order(d.tiles, b->order);
-            std::copy(o.begin(), o.end(), b->h_order.begin() + (long)at);
-            at += o.size();
-        }
-        if (total > b->order_cap) {
-            // the old table may still be read by queued runs: wait for them
-            e = cudaStreamSynchronize(s);
-            if (e == cudaSuccess) {
-                cudaFree(b->d_order);
-                b->d_order = nullptr;
-                b->order_cap = 0;
-                e = cudaMalloc(&b->d_order, sizeof(uint32_t) * (size_t)total);
-            }
-            if (e != cudaSuccess)
-                return cuda_fail(e, "allocating the tile order table");
-            b->order_cap = total;
-        }
-        // pageable source: the copy completes its host-side read before return
-        if (total > 0)
-            e = cudaMemcpyAsync(b->d_order, b->h_order.data(), sizeof(uint32_t) * (size_t)total,
-                                cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess)
-            return cuda_fail(e, "uploading the tile order");
-    }
-    b->beams.swap(nb);
-    b->total_tiles = (int)total;
-    b->graph_stale = true;
-    return HS_OK;
+    return batch_set_prepared(b, nb.data(), n_beams, reinterpret_cast<cudaStream_t>(stream));
 }
 
 hs_status hs_batch_run(hs_batch *b, hs_stream_t stream)

@@ -101,6 +101,14 @@ struct StagedBatch {
 bool staged_batch_available(const StagedShape &sh);
 int staged_batch_beams_per_launch(const StagedShape &sh);
 
+} // namespace hs
+struct hs_batch;
+namespace hs {
+// Install beams whose descriptors the caller encoded already (the serving
+// engine keeps one set per slot): uploads their tile order on s.
+hs_status batch_set_prepared(hs_batch *b, const StagedBatchBeam *beams, int n_beams,
+                             cudaStream_t s);
+
 // Shared host helpers (hs_api.cu)
 // Tile order of a plane of n_tiles tiles: 1 = linear, 2 = octave-interleaved.
 std::vector<uint32_t> tile_order(int n_tiles, int kind);

@@ -27,6 +27,8 @@
 
 #include "hs_internal.h"
 
+using namespace hs;
+
 namespace {
 
 // ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) ----------------------
@@ -55,20 +57,22 @@ constexpr int kSignalHarmonics = 16;
 
 // Exponential(mean 1) from 32 random bits: u = (r + 1/2) 2^-32 in (0, 1],
 // x = -ln u (at most ln 2^33 = 22.9, so tails used by thresholds of
-// false-alarm rate 1e-8 still occur); 0 - ln u keeps x = +0 at u = 1.
+// false-alarm rate 1e-8 still occur); 0 - ln u keeps x = +0 at u = 1.  The
+// hardware logarithm (__logf) is accurate enough for a noise source and
+// keeps the generator near the write bandwidth.
 __device__ __forceinline__ float exp1(uint32_t r)
 {
     const float u = fmaf((float)r, 2.3283064365386963e-10f, 1.1641532182693481e-10f);
-    return 0.0f - logf(u);
+    return fmaxf(0.0f - __logf(u), 0.0f);
 }
 
 // Noise plane, one Philox call per 4 consecutive bins of a row (grid.y = row).
 template <bool LOWP>
 __global__ void synth_noise(float *__restrict__ f32, __nv_bfloat16 *__restrict__ bf, long long n,
-                            long long ld, uint32_t k0, uint32_t k1)
+                            long long ld, long long width, uint32_t k0, uint32_t k1)
 {
     const int row = (int)blockIdx.y;
-    const long long quads = ld / 4;
+    const long long quads = width / 4; // bins [0, width) of the row are written
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < quads;
          q += (long long)gridDim.x * blockDim.x) {
         uint32_t c[4] = {(uint32_t)q, (uint32_t)(q >> 32), (uint32_t)row, kNoiseTag};
@@ -165,8 +169,10 @@ int64_t now_ns()
         .count();
 }
 
+// write_pad: also zero the bins [n, ld) of every row (otherwise only the
+// bins up to n rounded up to 4 are written).
 hs_status synth(void *fop, float *fop32, int dtype, int nt, long long n, long long ld,
-                uint64_t seed, int n_signals, cudaStream_t s)
+                uint64_t seed, int n_signals, cudaStream_t s, bool write_pad = true)
 {
     if (!fop || reinterpret_cast<uintptr_t>(fop) % 16 != 0 || nt < 1 || n < 1 || ld < n ||
         ld % 8 != 0 || n_signals < 0 || n_signals > kMaxSignals ||
@@ -179,14 +185,15 @@ hs_status synth(void *fop, float *fop32, int dtype, int nt, long long n, long lo
     float *f32 = dtype == HS_F32 ? static_cast<float *>(fop) : fop32;
     __nv_bfloat16 *bf = dtype == HS_BF16 ? static_cast<__nv_bfloat16 *>(fop) : nullptr;
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    const long long quads = ld / 4;
+    const long long width = write_pad ? ld : (n + 3) / 4 * 4;
+    const long long quads = width / 4;
     const int tpb = 256;
     const unsigned gx = (unsigned)std::min<long long>((quads + tpb - 1) / tpb, 1 << 16);
     const dim3 grid(gx, (unsigned)nt);
     if (bf)
-        synth_noise<true><<<grid, tpb, 0, s>>>(f32, bf, n, ld, k0, k1);
+        synth_noise<true><<<grid, tpb, 0, s>>>(f32, bf, n, ld, width, k0, k1);
     else
-        synth_noise<false><<<grid, tpb, 0, s>>>(f32, bf, n, ld, k0, k1);
+        synth_noise<false><<<grid, tpb, 0, s>>>(f32, bf, n, ld, width, k0, k1);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && n_signals > 0) {
         synth_signals<<<1, 1, 0, s>>>(f32, bf, nt, n, ld, draw_signals(seed, n, n_signals));
@@ -207,6 +214,7 @@ struct Req {
 struct Group {
     std::vector<Req> reqs;
     int id = 0;
+    int lane = 0; // stream index
     hs_status err = HS_OK;
     cudaEvent_t ev = nullptr;
 };
@@ -225,12 +233,18 @@ struct hs_server {
     long long ld_max = 0;
     float *d_f32 = nullptr;            // [n_slots][nt][ld_max] FP32 plane or FP32 copy
     __nv_bfloat16 *d_bf = nullptr;     // [n_slots][nt][ld_max] BF16 plane
-    hs_cand *d_rec = nullptr;          // [n_slots][cap]
-    uint32_t *d_cnt = nullptr;         // [n_slots][2]
-    hs_cand *h_rec = nullptr;          // pinned mirrors
-    uint32_t *h_cnt = nullptr;
-    hs_batch *batch[2] = {nullptr, nullptr}; // FP32, BF16
-    cudaStream_t stream = nullptr;
+    // per slot: 16 bytes of counters, then cand_capacity records; the
+    // pinned host mirror has the same layout, so one copy returns a result
+    unsigned char *d_out = nullptr;
+    unsigned char *h_out = nullptr;
+    size_t out_stride = 0;
+    // per slot and dtype, the descriptors of the slot's plane (pitch ld_max)
+    std::vector<StagedBatchBeam> slot_beam[2];
+    // groups alternate between two streams, each with its own batches, so
+    // one group's plane generation overlaps the previous group's summing
+    static constexpr int kStreams = 2;
+    cudaStream_t stream[kStreams] = {nullptr, nullptr};
+    hs_batch *batch[kStreams][2] = {{nullptr, nullptr}, {nullptr, nullptr}}; // [stream][FP32, BF16]
 
     std::mutex mu;
     std::condition_variable cv_dispatch, cv_complete, cv_done;
@@ -246,41 +260,54 @@ struct hs_server {
     bool stop_dispatch = false, stop_complete = false;
     hs_server_stats st{};
     std::thread dispatcher, completer;
+    int tile_order = 1; // linear: no per-group order table to build and upload
 };
 
 namespace {
+
+uint32_t *slot_counters(unsigned char *base, size_t stride, int slot)
+{
+    return reinterpret_cast<uint32_t *>(base + stride * (size_t)slot);
+}
+
+hs_cand *slot_records(unsigned char *base, size_t stride, int slot)
+{
+    return reinterpret_cast<hs_cand *>(base + stride * (size_t)slot + 16);
+}
 
 void launch_group(hs_server *s, Group &g)
 {
     const int nt = s->cfg.n_templates;
     const uint32_t cap = s->cfg.cand_capacity;
     const size_t slot_elems = (size_t)nt * (size_t)s->ld_max;
-    std::vector<hs_beam> beams[2];
+    cudaStream_t st_ = s->stream[g.lane];
+    std::vector<StagedBatchBeam> beams[2];
     hs_status st = HS_OK;
     for (const Req &r : g.reqs) {
-        const long long n = r.r.n_bins, ld = round8(n);
+        const long long n = r.r.n_bins;
+        const bool lowp = r.r.dtype == HS_BF16;
         float *f32 = s->d_f32 + slot_elems * r.slot;
         __nv_bfloat16 *bf = s->d_bf + slot_elems * r.slot;
-        const bool lowp = r.r.dtype == HS_BF16;
         if (st == HS_OK)
-            st = synth(lowp ? (void *)bf : (void *)f32, lowp ? f32 : nullptr, r.r.dtype, nt, n, ld,
-                       r.r.seed, r.r.n_signals, s->stream);
-        hs_beam b{};
-        b.fop = lowp ? (const void *)bf : (const void *)f32;
-        b.fop32 = lowp ? f32 : nullptr;
-        b.n_bins = n;
-        b.ld = ld;
-        b.cands.records = s->d_rec + (size_t)cap * r.slot;
-        b.cands.count = s->d_cnt + 2 * r.slot;
-        b.cands.capacity = cap;
-        beams[lowp ? 1 : 0].push_back(b);
+            st = synth(lowp ? (void *)bf : (void *)f32, lowp ? f32 : nullptr, r.r.dtype, nt, n,
+                       s->ld_max, r.r.seed, r.r.n_signals, st_, false);
+        StagedBatchBeam d = s->slot_beam[lowp ? 1 : 0][(size_t)r.slot];
+        d.fop32 = lowp ? f32 : nullptr;
+        d.n = n;
+        d.ld = s->ld_max;
+        d.rec = slot_records(s->d_out, s->out_stride, r.slot);
+        d.counters = slot_counters(s->d_out, s->out_stride, r.slot);
+        d.cap = cap;
+        d.tiles = (int)((n + 127) / 128);
+        beams[lowp ? 1 : 0].push_back(d);
     }
     for (int d = 0; d < 2 && st == HS_OK; ++d) {
         if (beams[d].empty())
             continue;
-        st = hs_batch_set_beams(s->batch[d], beams[d].data(), (int)beams[d].size(), s->stream);
+        hs_batch *b = s->batch[g.lane][d];
+        st = batch_set_prepared(b, beams[d].data(), (int)beams[d].size(), st_);
         if (st == HS_OK)
-            st = hs_batch_run(s->batch[d], s->stream);
+            st = hs_batch_run(b, reinterpret_cast<hs_stream_t>(st_));
         if (st != HS_OK)
             g_err = hs_batch_last_error();
     }
@@ -288,14 +315,11 @@ void launch_group(hs_server *s, Group &g)
     for (const Req &r : g.reqs) {
         if (st != HS_OK || e != cudaSuccess)
             break;
-        e = cudaMemcpyAsync(s->h_cnt + 2 * r.slot, s->d_cnt + 2 * r.slot, 2 * sizeof(uint32_t),
-                            cudaMemcpyDeviceToHost, s->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(s->h_rec + (size_t)cap * r.slot, s->d_rec + (size_t)cap * r.slot,
-                                sizeof(hs_cand) * cap, cudaMemcpyDeviceToHost, s->stream);
+        e = cudaMemcpyAsync(s->h_out + s->out_stride * r.slot, s->d_out + s->out_stride * r.slot,
+                            s->out_stride, cudaMemcpyDeviceToHost, st_);
     }
     if (st == HS_OK && e == cudaSuccess)
-        e = cudaEventRecord(g.ev, s->stream);
+        e = cudaEventRecord(g.ev, st_);
     if (st == HS_OK && e != cudaSuccess)
         st = cuda_fail(e, "serving group");
     g.err = st;
@@ -325,6 +349,7 @@ void dispatcher_main(hs_server *s)
                 g.reqs.push_back(r);
             }
             g.id = s->n_groups++;
+            g.lane = g.id % hs_server::kStreams;
             s->in_flight += take;
             if (s->events.empty()) {
                 g.ev = nullptr;
@@ -340,7 +365,9 @@ void dispatcher_main(hs_server *s)
         } else {
             launch_group(s, g);
         }
+        const int64_t t1 = now_ns();
         std::lock_guard<std::mutex> lk(s->mu);
+        s->st.dispatch_ns += (uint64_t)(t1 - g.reqs.front().t_admit);
         s->inflight.push_back(std::move(g));
         s->st.groups++;
         s->cv_complete.notify_one();
@@ -381,10 +408,11 @@ void completer_main(hs_server *s)
             if (gs != HS_OK) {
                 d.res.status = gs;
             } else {
-                const uint32_t cnt = s->h_cnt[2 * r.slot], dev = s->h_cnt[2 * r.slot + 1];
+                const uint32_t *c = slot_counters(s->h_out, s->out_stride, r.slot);
+                const uint32_t cnt = c[0], dev = c[1];
                 d.res.n_cands = cnt;
                 d.res.status = dev != 0u ? (hs_status)dev : cnt > cap ? HS_ERR_OVERFLOW : HS_OK;
-                const hs_cand *src = s->h_rec + (size_t)cap * r.slot;
+                const hs_cand *src = slot_records(s->h_out, s->out_stride, r.slot);
                 d.recs.assign(src, src + std::min(cnt, cap));
                 points += (uint64_t)s->cfg.n_templates * (uint64_t)r.r.n_bins;
             }
@@ -407,20 +435,21 @@ void completer_main(hs_server *s)
 
 void free_server(hs_server *s)
 {
-    if (s->stream)
-        cudaStreamSynchronize(s->stream);
-    for (hs_batch *b : s->batch)
-        hs_batch_destroy(b);
+    for (cudaStream_t st : s->stream)
+        if (st)
+            cudaStreamSynchronize(st);
+    for (auto &lane : s->batch)
+        for (hs_batch *b : lane)
+            hs_batch_destroy(b);
     for (cudaEvent_t e : s->events)
         cudaEventDestroy(e);
     cudaFree(s->d_f32);
     cudaFree(s->d_bf);
-    cudaFree(s->d_rec);
-    cudaFree(s->d_cnt);
-    cudaFreeHost(s->h_rec);
-    cudaFreeHost(s->h_cnt);
-    if (s->stream)
-        cudaStreamDestroy(s->stream);
+    cudaFree(s->d_out);
+    cudaFreeHost(s->h_out);
+    for (cudaStream_t st : s->stream)
+        if (st)
+            cudaStreamDestroy(st);
     delete s;
 }
 
@@ -459,36 +488,56 @@ hs_status hs_server_create(hs_server **out, const hs_server_config *cfg)
     s->ld_max = round8(c.slot_bins);
     cudaGetDevice(&s->device);
     const int group = c.max_group > 0 ? c.max_group : c.n_slots;
-    for (int d = 0; d < 2; ++d) {
-        hs_options o{};
-        o.dtype = d == 0 ? HS_F32 : HS_BF16;
-        const hs_status st = hs_batch_create(&s->batch[d], c.n_templates, c.H, s->ta.data(), &o,
-                                             group);
-        if (st != HS_OK) {
-            g_err = hs_batch_last_error();
-            free_server(s);
-            return st;
+    for (int l = 0; l < hs_server::kStreams; ++l)
+        for (int d = 0; d < 2; ++d) {
+            hs_options o{};
+            o.dtype = d == 0 ? HS_F32 : HS_BF16;
+            o.order = s->tile_order;
+            const hs_status st = hs_batch_create(&s->batch[l][d], c.n_templates, c.H,
+                                                 s->ta.data(), &o, group);
+            if (st != HS_OK) {
+                g_err = hs_batch_last_error();
+                free_server(s);
+                return st;
+            }
         }
-    }
     const size_t elems = (size_t)c.n_slots * c.n_templates * (size_t)s->ld_max;
     cudaError_t e = cudaMalloc(&s->d_f32, elems * sizeof(float));
     if (e == cudaSuccess)
         e = cudaMalloc(&s->d_bf, elems * sizeof(__nv_bfloat16));
+    s->out_stride = 16 + sizeof(hs_cand) * (size_t)c.cand_capacity;
     if (e == cudaSuccess)
-        e = cudaMalloc(&s->d_rec, sizeof(hs_cand) * c.cand_capacity * (size_t)c.n_slots);
+        e = cudaMalloc(&s->d_out, s->out_stride * (size_t)c.n_slots);
     if (e == cudaSuccess)
-        e = cudaMalloc(&s->d_cnt, sizeof(uint32_t) * 2 * (size_t)c.n_slots);
-    if (e == cudaSuccess)
-        e = cudaMallocHost(&s->h_rec, sizeof(hs_cand) * c.cand_capacity * (size_t)c.n_slots);
-    if (e == cudaSuccess)
-        e = cudaMallocHost(&s->h_cnt, sizeof(uint32_t) * 2 * (size_t)c.n_slots);
-    if (e == cudaSuccess)
-        e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+        e = cudaMallocHost(&s->h_out, s->out_stride * (size_t)c.n_slots);
+    for (int l = 0; l < hs_server::kStreams && e == cudaSuccess; ++l)
+        e = cudaStreamCreateWithFlags(&s->stream[l], cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         const hs_status st = cuda_fail(e, "reserving the server's slots");
         free_server(s);
         return st;
     }
+    // descriptors of every slot's plane, encoded once: the plane of a
+    // request of n bins keeps the slot's pitch, bins >= n are never summed
+    const StagedShape sh32{c.n_templates, c.H, 128, HS_F32}, sh16{c.n_templates, c.H, 128, HS_BF16};
+    for (int d = 0; d < 2; ++d)
+        s->slot_beam[d].resize((size_t)c.n_slots);
+    for (int i = 0; i < c.n_slots; ++i)
+        for (int d = 0; d < 2; ++d) {
+            StagedBatchBeam &b = s->slot_beam[d][(size_t)i];
+            std::memset(&b, 0, sizeof b);
+            const void *base = d == 0 ? (const void *)(s->d_f32 + (size_t)i * c.n_templates * s->ld_max)
+                                      : (const void *)(s->d_bf + (size_t)i * c.n_templates * s->ld_max);
+            for (int m = 1; m <= c.H; ++m) {
+                int w = 0, rows = 0;
+                staged_box(d == 0 ? sh32 : sh16, m, &w, &rows);
+                if (encode_tensor_map(&b.maps[m - 1], d == 0 ? HS_F32 : HS_BF16, base, s->ld_max,
+                                      s->ld_max, c.n_templates, w, rows) != CUDA_SUCCESS) {
+                    free_server(s);
+                    return fail(HS_ERR_CUDA, "cuTensorMapEncodeTiled failed for a slot");
+                }
+            }
+        }
     for (int i = c.n_slots - 1; i >= 0; --i)
         s->free_slots.push_back(i);
     s->st.free_slots = c.n_slots;

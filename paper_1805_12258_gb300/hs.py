@@ -89,7 +89,8 @@ class hs_result(ctypes.Structure):
 class hs_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
                 ("completed", ctypes.c_uint64), ("groups", ctypes.c_uint64),
-                ("points", ctypes.c_uint64), ("queued", ctypes.c_int32),
+                ("points", ctypes.c_uint64), ("dispatch_ns", ctypes.c_uint64),
+                ("queued", ctypes.c_int32),
                 ("in_flight", ctypes.c_int32), ("free_slots", ctypes.c_int32),
                 ("peak_queue", ctypes.c_int32)]
 
