@@ -88,6 +88,9 @@ struct Cfg {
         return o;
     }
     static constexpr int SMEM = OFF(H + 1);
+    // CTAs that fit on an SM by shared memory (228 KB, 1 KB reserved per
+    // CTA), at most 8
+    static constexpr int CTAS_SMEM = cmin(8, 233472 / (SMEM + 1024 + 64));
     static constexpr int TX()
     {
         int t = 0;
@@ -318,16 +321,20 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
     return true;
 }
 
-// CTAs per SM the register budget is sized for
-#ifndef HS_STAGED_MINB
-#define HS_STAGED_MINB 3
-#endif
+// Resident CTAs the register budget is sized for: as many as shared memory
+// allows while each thread keeps 128 registers (the fast pass holds 16
+// packed row-pair values, 16 span indices and the group bounds).
+template <int NT, int H, int TB, typename T>
+constexpr int resident_ctas()
+{
+    return cmin(Cfg<NT, H, TB, T>::CTAS_SMEM, 65536 / (TB * 128));
+}
 
 // One plane.  Grid-stride over the tile order: with one CTA per tile each CTA
 // sums one tile; with a smaller grid the CTAs stay resident and walk several
 // tiles, saving the launch and teardown of a CTA per tile.
 template <int NT, int H, int TB, typename T>
-__global__ void __launch_bounds__(TB, HS_STAGED_MINB * 128 / TB)
+__global__ void __launch_bounds__(TB, (resident_ctas<NT, H, TB, T>()))
     staged_kernel(const __grid_constant__ Params<NT, H, T> p)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -392,7 +399,7 @@ struct BatchParams {
 // CTA when the grid covers them) and find each tile's beam by a CTA-uniform
 // scan of the cumulative tile ends.
 template <int NT, int H, int TB, typename T>
-__global__ void __launch_bounds__(TB, HS_STAGED_MINB * 128 / TB)
+__global__ void __launch_bounds__(TB, (resident_ctas<NT, H, TB, T>()))
     batched_kernel(const __grid_constant__ BatchParams<NT, H, T> p)
 {
     extern __shared__ __align__(1024) unsigned char smem[];

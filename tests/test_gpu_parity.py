@@ -204,13 +204,26 @@ def test_long_tile_walk_matches_generic():
     assert na == nb > 0 and np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("tb", [64, 96])
+@pytest.mark.parametrize("tb", [128, 64, 96])
 def test_tile_widths_same_result(tb):
-    plane = synth.noise(85, 20000, seed=11)
+    # every compiled tile width gives the generic kernel's records, with a
+    # ragged last tile in padded rows and patches of negative inputs (whose
+    # pairs take the exact pass)
+    n = 20011
+    plane = synth.noise(85, n, seed=11)
+    plane[3, 100:300] *= -1.0
+    plane[60, 5000:5100] *= -1.0
     ta = synth.thresholds(1e-4, 16, 85)
-    a, _, _, _ = run_gpu(plane, 16, ta)
-    b, _, _, used = run_gpu(plane, 16, ta, tile_bins=tb)
-    assert used == "staged" and np.array_equal(a, b)
+    a, na, _, _ = run_gpu(plane, 16, ta, kernel="generic")
+    padded = torch.zeros((85, n + 1), dtype=torch.float32, device="cuda")  # 16-byte rows
+    padded[:, :n] = torch.from_numpy(plane).cuda()
+    cands = hs.CandBuffer(1 << 20)
+    with hs.Plan(85, n, 16, ta, tile_bins=tb, row_pitch=n + 1) as plan:
+        assert plan.kernel == "staged"
+        plan.run(padded, cands)
+        b, nb, st = cands.fetch()
+    assert st == hs.HS_OK
+    assert na == nb > 0 and np.array_equal(a, b)
 
 
 @pytest.mark.parametrize("kernel", ["staged", "generic"])
