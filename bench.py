@@ -58,6 +58,10 @@ def parse():
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--order", type=int, default=0)
     ap.add_argument("--tile-bins", type=int, default=0)
+    ap.add_argument("--stages", type=int, default=0,
+                    help="staged kernel: ring stages of the pipelined variant (0: one CTA per tile)")
+    ap.add_argument("--z-split", type=int, default=0,
+                    help="pipelined variant: threads per bin (0 default)")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU work of the oracle sample (core-seconds)")
@@ -280,7 +284,7 @@ def run_ours(args):
     fop32 = fop if args.dtype == "f32" else host32.cuda()
     cands = hs.CandBuffer(1 << 20)
     plan = hs.Plan(nt, n, H, ta, dtype=args.dtype, order=args.order, tile_bins=args.tile_bins,
-                   grid_per_sm=args.grid_per_sm)
+                   grid_per_sm=args.grid_per_sm, stages=args.stages, z_split=args.z_split)
     stream = torch.cuda.current_stream()
 
     def step():

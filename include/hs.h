@@ -78,6 +78,10 @@ typedef struct {
                        that walk the tiles */
     int row_pitch;  /* elements between plane rows (0 = n_bins); >= n_bins.  The staged
                        kernel needs row_pitch * element size to be a multiple of 16 bytes */
+    int stages;     /* staged kernel: 0 = one CTA per tile (or grid_per_sm); s > 0 = one
+                       persistent CTA per SM with an s-stage ring of tiles, filled by a
+                       producer warp while consumer groups sum */
+    int z_split;    /* with stages > 0: consumer groups of tile_bins threads (0 = 2) */
 } hs_options;
 
 /* Candidate record flags */

@@ -26,6 +26,7 @@ struct hs_plan {
     int device = 0;
     int kernel = HS_KERNEL_GENERIC;
     int tb = 128;
+    int ring_zs = 0, ring_stages = 0; // pipelined staged kernel (0: one CTA per tile)
     int groups = 0;
     int n_tiles = 0;
     float delta = 0.f;     // relative error bound of 16-bit storage
@@ -226,6 +227,8 @@ hs_status launch_range(hs_plan *p, const void *fop, const float *fop32, cudaStre
         L.tile_lo = (int)(f_lo / p->tb);
         L.tile_hi = (int)((f_hi + p->tb - 1) / p->tb);
         L.grid_per_sm = p->opt.grid_per_sm;
+        L.ring_zs = p->ring_zs;
+        L.ring_stages = p->ring_stages;
         e = launch_staged(L, s);
         if (e != cudaSuccess)
             return cuda_fail(e, "staged kernel launch");
@@ -303,7 +306,8 @@ hs_status hs_plan_create(hs_plan **out, int n_templates, int64_t n_bins, int H,
         return fail(HS_ERR_INVALID, "thresholds is null");
     if (o.dtype < HS_F32 || o.dtype > HS_F16 || o.index < 0 || o.index > 1 || o.zround < 0 ||
         o.zround > 1 || o.kernel < 0 || o.kernel > 2 || o.order < 0 || o.order > 2 ||
-        o.tile_bins < 0 || o.grid_per_sm < 0 || o.grid_per_sm > 64)
+        o.tile_bins < 0 || o.grid_per_sm < 0 || o.grid_per_sm > 64 || o.stages < 0 ||
+        o.stages > 8 || o.z_split < 0 || o.z_split > 8)
         return fail(HS_ERR_INVALID, "unknown option value");
     if (o.row_pitch != 0 && o.row_pitch < n_bins)
         return fail(HS_ERR_INVALID, "row_pitch must be 0 or at least n_bins");
@@ -346,6 +350,18 @@ hs_status hs_plan_create(hs_plan **out, int n_templates, int64_t n_bins, int H,
         p->tb = 128;
     } else {
         p->kernel = HS_KERNEL_STAGED;
+        if (o.stages > 0) {
+            const int zs = o.z_split ? o.z_split : 2;
+            if (!ring_available(sh, zs, o.stages)) {
+                delete p;
+                return fail(HS_ERR_UNSUPPORTED, "no pipelined staged kernel for this shape, "
+                                                "consumer groups and stages (compiled: 85x16 "
+                                                "FP32: 128 bins with 2 or 3 groups and 3 stages, "
+                                                "96 bins with 2 or 4 groups and 4 stages)");
+            }
+            p->ring_zs = zs;
+            p->ring_stages = o.stages;
+        }
     }
 
     cudaError_t e = cudaMalloc(&p->d_ta, sizeof(float) * p->ta.size());

@@ -123,6 +123,34 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
     return done != 0u;
 }
 
+// Plain arrival (no transaction bytes) on a barrier.
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Named barrier `id` (1..15) over `count` threads (a multiple of 32): every
+// participating thread gets the OR of `v` over the group.
+__device__ __forceinline__ bool group_or(int id, int count, bool v)
+{
+    uint32_t r;
+    __syncwarp();
+    asm volatile("{\n\t.reg .pred p, q;\n\t"
+                 "setp.ne.u32 q, %1, 0;\n\t"
+                 "bar.red.or.pred p, %2, %3, q;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(r)
+                 : "r"((uint32_t)v), "r"(id), "r"(count)
+                 : "memory");
+    return r != 0u;
+}
+
+__device__ __forceinline__ void group_sync(int id, int count)
+{
+    __syncwarp();
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
 // Wait for phase `parity` of the barrier for at most limit_ns nanoseconds.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
                                                   uint64_t limit_ns)

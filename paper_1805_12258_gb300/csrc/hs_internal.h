@@ -68,7 +68,11 @@ struct StagedLaunch {
     long long ld;             // row pitch of the plane and its FP32 copy (elements)
     int tile_lo, tile_hi;     // tiles [tile_lo, tile_hi) of the order
     int grid_per_sm;          // 0: one CTA per tile; k > 0: k resident CTAs per SM
+    int ring_zs, ring_stages; // > 0: the pipelined kernel, consumer groups and stages
 };
+
+// True when the pipelined kernel is compiled for this shape, groups and stages.
+bool ring_available(const StagedShape &sh, int groups, int stages);
 
 cudaError_t launch_staged(const StagedLaunch &a, cudaStream_t s);
 

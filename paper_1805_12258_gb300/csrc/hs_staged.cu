@@ -177,14 +177,20 @@ __device__ __forceinline__ void issue_tile(const TileTarget &tt, int f0, uint32_
 // Wait for the tile's stage (phase `parity` of `bar`), run the fast pass and
 // the slow pass, append the hits to tt's buffer.  Called by every thread of
 // the CTA; returns false (CTA-uniformly) if the stage did not arrive in time.
-template <int NT, int H, int TB, typename T, typename P>
+// any_of(v) returns the OR of v over the threads that sum the tile (the CTA,
+// or one consumer group of the pipelined kernel) and synchronises them.
+struct CtaOr {
+    __device__ __forceinline__ bool operator()(bool v) const { return __syncthreads_or(v) != 0; }
+};
+
+template <int NT, int H, int TB, typename T, typename P, typename AnyOf = CtaOr>
 __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
                                          int f0, const unsigned char *smem, uint32_t bar,
-                                         uint32_t parity)
+                                         uint32_t parity, AnyOf any_of = AnyOf{})
 {
     using C = Cfg<NT, H, TB, T>;
     constexpr int Z = C::Z;
-    const int tid = threadIdx.x;
+    const int tid = (int)threadIdx.x % TB;
 
     // This thread's column in every span, as an element index of the centre
     // row (template z = 0), computed while the copies are in flight.
@@ -199,7 +205,7 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
     });
 
     // CTA-uniform outcome of the bounded wait for the stage
-    const bool ok = __syncthreads_or(!mbar_wait_bounded(bar, parity, kWaitLimitNs)) == 0;
+    const bool ok = !any_of(!mbar_wait_bounded(bar, parity, kWaitLimitNs));
 
     // ---- fast pass: every row pair, group prefilter ------------------------------
     // d = HP_b - bound has its sign bit set exactly when HP_b < bound (IEEE
@@ -359,6 +365,93 @@ __global__ void __launch_bounds__(TB, (resident_ctas<NT, H, TB, T>()))
     }
 }
 
+// One plane, pipelined and warp-specialised: one persistent CTA per SM with
+// an S-stage ring of tile stages.  A producer warp issues each tile's boxes
+// as soon as its stage is released; NC consumer groups of TB threads sum the
+// tiles (group c takes iterations c, c + NC, ...), so the copies of the next
+// tiles are in flight while the groups sum.  full[s] completes once per use
+// of stage s (the boxes landed), empty[s] once per release.  Iteration j uses
+// stage j % S in its phase k = j / S.  Before waiting on full[s] for phase k a
+// consumer waits on empty[s] for phase k - 1, so a parity it waits for is
+// never that of a phase two behind (2 S is a multiple of NC: iteration j - 2S
+// belongs to the same group, which released it already).
+template <int NT, int H, int TB, int NC, int S, typename T>
+__global__ void __launch_bounds__(NC *TB + 32, 1)
+    pipe_kernel(const __grid_constant__ Params<NT, H, T> p)
+{
+    static_assert((2 * S) % NC == 0 && S >= 2 && NC >= 1, "ring shape");
+    using C = Cfg<NT, H, TB, T>;
+    constexpr int STAGE = round_up(C::SMEM, 1024);
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full_bar[S], empty_bar[S];
+    __shared__ int issued; // iterations the producer issued
+    const uint32_t sbase = smem_addr(smem);
+    const TileTarget tt{p.maps, p.fop32, p.n, p.ld, p.rec, p.counters, p.cap};
+    const int G = (int)gridDim.x;
+    const int n_it = (int)blockIdx.x < p.n_slots ? (p.n_slots - 1 - (int)blockIdx.x) / G + 1 : 0;
+    auto tile_f0 = [&](int j) {
+        const int slot = p.tile_lo + (int)blockIdx.x + j * G;
+        return (p.order ? (int)__ldg(p.order + slot) : slot) * TB;
+    };
+    if (threadIdx.x == 0) {
+        static_for<0, H>([&](auto M) { prefetch_tmap(&p.maps[M]); });
+        static_for<0, S>([&](auto st) {
+            mbar_init(smem_addr(&full_bar[st]), 1);
+            mbar_init(smem_addr(&empty_bar[st]), 1);
+        });
+        issued = 0;
+    }
+    __syncthreads();
+    const int group = (int)threadIdx.x / TB;
+    if (group == NC) { // producer warp
+        if ((threadIdx.x & 31u) == 0u) {
+            for (int j = 0; j < n_it; ++j) {
+                const int st = j % S, k = j / S;
+                if (k >= 1 && !mbar_wait_bounded(smem_addr(&empty_bar[st]), (uint32_t)(k - 1) & 1u,
+                                                 kWaitLimitNs)) {
+                    set_status(p.counters, HS_ERR_TIMEOUT);
+                    break;
+                }
+                issue_tile<NT, H, TB, T>(tt, tile_f0(j), sbase + st * STAGE,
+                                         smem_addr(&full_bar[st]));
+                *(volatile int *)&issued = j + 1;
+            }
+        }
+        __syncwarp();
+    } else { // consumer group
+        const int gid = 1 + group;
+        auto any_of = [gid](bool v) { return group_or(gid, TB, v); };
+        for (int j = group; j < n_it; j += NC) {
+            const int st = j % S, k = j / S;
+            const uint32_t full = smem_addr(&full_bar[st]), empty = smem_addr(&empty_bar[st]);
+            if (k >= 1 && any_of(!mbar_wait_bounded(empty, (uint32_t)(k - 1) & 1u, kWaitLimitNs))) {
+                if (threadIdx.x % TB == 0)
+                    set_status(p.counters, HS_ERR_TIMEOUT);
+                break;
+            }
+            if (!sum_tile<NT, H, TB, T>(p, tt, tile_f0(j), smem + st * STAGE, full,
+                                        (uint32_t)k & 1u, any_of))
+                break;
+            group_sync(gid, TB); // the group is done with stage st
+            if (threadIdx.x % TB == 0)
+                mbar_arrive(empty);
+        }
+    }
+    __syncthreads();
+    // after a timeout, let every issued copy land before the CTA exits
+    if (threadIdx.x == 0) {
+        const int n_issued = *(volatile int *)&issued;
+        for (int st = 0; st < S; ++st) {
+            int last = -1;
+            for (int j = st; j < n_issued; j += S)
+                last = j;
+            if (last >= 0)
+                mbar_wait_bounded(smem_addr(&full_bar[st]), (uint32_t)(last / S) & 1u,
+                                  kWaitLimitNs);
+        }
+    }
+}
+
 // One beam of a batched launch, carried in the kernel parameters: its
 // descriptors, size, output, and the end of its tiles in the launch's slots.
 template <int H>
@@ -489,6 +582,47 @@ cudaError_t launch_one(const StagedLaunch &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+template <int NT, int H, int TB, int NC, int S, typename T>
+cudaError_t launch_pipe(const StagedLaunch &a, cudaStream_t s)
+{
+    using C = Cfg<NT, H, TB, T>;
+    constexpr int SMEM = S * round_up(C::SMEM, 1024);
+    static_assert(SMEM <= 232448 - 2048, "ring stages exceed the shared memory of a CTA");
+    Params<NT, H, T> p;
+    std::memset(&p, 0, sizeof p);
+    std::memcpy(p.maps, a.maps, sizeof(CUtensorMap) * H);
+    for (int g = 0; g < C::G; ++g)
+        p.tmin[g] = a.tmin_host[g];
+    p.ta = a.ta;
+    p.fop32 = a.fop32;
+    p.order = a.order;
+    p.rec = a.rec;
+    p.counters = a.counters;
+    p.cap = a.cap;
+    p.delta = a.delta;
+    p.band_abs = a.band_abs;
+    p.n = a.n;
+    p.ld = a.ld;
+    p.tile_lo = a.tile_lo;
+    p.n_slots = a.tile_hi - a.tile_lo;
+    if (p.n_slots <= 0)
+        return cudaSuccess;
+    auto kern = pipe_kernel<NT, H, TB, NC, S, T>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess)
+        return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess)
+        return e;
+    const int grid = sms < p.n_slots ? sms : p.n_slots;
+    kern<<<grid, NC * TB + 32, SMEM, s>>>(p);
+    return cudaGetLastError();
+}
+
 template <int NT, int H, int TB, typename T>
 cudaError_t launch_batch_one(const StagedBatch &a, cudaStream_t s)
 {
@@ -573,6 +707,14 @@ void box_of(int m, int *w, int *rows)
     X(21, 8, 128, __nv_bfloat16, HS_BF16)                                                     \
     X(21, 8, 128, __half, HS_F16)
 
+// Pipelined variants: (templates, levels, tile bins, consumer groups,
+// stages, type).
+#define HS_PIPE_SHAPES(X)                                                                     \
+    X(85, 16, 128, 2, 3, float, HS_F32)                                                       \
+    X(85, 16, 128, 3, 3, float, HS_F32)                                                       \
+    X(85, 16, 96, 2, 4, float, HS_F32)                                                        \
+    X(85, 16, 96, 4, 4, float, HS_F32)
+
 // Shapes with a batched kernel (tile width 128).
 #define HS_BATCH_SHAPES(X)                                                                    \
     X(85, 16, 128, float, HS_F32)                                                             \
@@ -653,8 +795,29 @@ int staged_groups(int H, int *ends)
     return g;
 }
 
+bool ring_available(const StagedShape &sh, int groups, int stages)
+{
+#define R(NT_, H_, TB_, NC_, S_, T_, DT_)                                                     \
+    if (sh.nt == NT_ && sh.H == H_ && sh.tb == TB_ && sh.dtype == DT_ && groups == NC_ &&    \
+        stages == S_)                                                                         \
+        return true;
+    HS_PIPE_SHAPES(R)
+#undef R
+    return false;
+}
+
 cudaError_t launch_staged(const StagedLaunch &a, cudaStream_t s)
 {
+    if (a.ring_zs > 0) {
+        const StagedShape &sh = a.sh;
+#define R(NT_, H_, TB_, NC_, S_, T_, DT_)                                                     \
+        if (sh.nt == NT_ && sh.H == H_ && sh.tb == TB_ && sh.dtype == DT_ &&                  \
+            a.ring_zs == NC_ && a.ring_stages == S_)                                          \
+            return launch_pipe<NT_, H_, TB_, NC_, S_, T_>(a, s);
+        HS_PIPE_SHAPES(R)
+#undef R
+        return cudaErrorInvalidValue;
+    }
     const StagedShape &sh = a.sh;
 #define X(NT_, H_, TB_, T_, DT_)                                                              \
     if (sh.nt == NT_ && sh.H == H_ && sh.tb == TB_ && sh.dtype == DT_)                       \

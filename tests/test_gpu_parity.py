@@ -226,6 +226,41 @@ def test_tile_widths_same_result(tb):
     assert na == nb > 0 and np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("tb,groups,stages", [(128, 2, 3), (128, 3, 3), (96, 2, 4), (96, 4, 4)])
+def test_pipelined_variants_same_result(tb, groups, stages):
+    # the persistent pipelined kernel (a producer warp filling a ring of
+    # stages that wraps many times, consumer groups summing) gives the
+    # generic kernel's records, with a ragged last tile in padded rows and
+    # patches of negative inputs
+    n = (1 << 18) + 37
+    plane = synth.noise(85, n, seed=17)
+    plane[0, 1000:1300] *= -1.0
+    plane[84, 70000:70100] *= -1.0
+    ta = synth.thresholds(1e-4, 16, 85)
+    a, na, _, _ = run_gpu(plane, 16, ta, kernel="generic")
+    ld = n + 3
+    padded = torch.zeros((85, ld), dtype=torch.float32, device="cuda")
+    padded[:, :n] = torch.from_numpy(plane).cuda()
+    cands = hs.CandBuffer(1 << 20)
+    with hs.Plan(85, n, 16, ta, tile_bins=tb, stages=stages, z_split=groups,
+                 row_pitch=ld) as plan:
+        assert plan.kernel == "staged"
+        plan.run(padded, cands)
+        b, nb, st = cands.fetch()
+    assert st == hs.HS_OK
+    assert na == nb > 0 and np.array_equal(a, b)
+
+
+def test_pipelined_matches_oracle_on_the_small_ska_slice():
+    n = 1 << 16
+    plane = synth.noise(85, n, seed=23)
+    ta = synth.thresholds(1e-5, 16, 85)
+    recs, cnt, st, used = run_gpu(plane, 16, ta, stages=3)
+    assert used == "staged" and st == hs.HS_OK
+    ref, near = oracle.detect(plane, 16, ta, threads=8)
+    assert_matches_oracle(recs, ref, near)
+
+
 @pytest.mark.parametrize("kernel", ["staged", "generic"])
 def test_run_host_matches_run(kernel):
     wl = synth.small_plane(seed=2)
