@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--beams", type=int, default=64)
     ap.add_argument("--beam-log2", default="18,22",
                     help="batch workload: beam lengths log-uniform in [2^lo, 2^hi] bins")
-    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"])
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"])
     ap.add_argument("--order", type=int, default=0)
     ap.add_argument("--tile-bins", type=int, default=0)
     ap.add_argument("--stages", type=int, default=0,
@@ -279,7 +279,8 @@ def run_ours(args):
     if args.dtype == "f32":
         host = host32
     else:
-        host = host32.to(torch.bfloat16).pin_memory()
+        lowp = torch.bfloat16 if args.dtype == "bf16" else torch.float16
+        host = host32.to(lowp).pin_memory()
     fop = host.cuda()
     fop32 = fop if args.dtype == "f32" else host32.cuda()
     cands = hs.CandBuffer(1 << 20)
