@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ska", choices=["ska", "small", "batch", "serve"])
+    ap.add_argument("--shard", default="planes", choices=["planes", "band"],
+                    help="N > 1: each rank sums its own plane (weak scaling), or one band "
+                         "of the bins of the same plane (strong scaling)")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="serve workload: length of the Poisson arrival phase")
     ap.add_argument("--serve-rate", type=float, default=1000.0, help="arrivals per second")
@@ -259,7 +262,7 @@ def run_ours(args):
     import torch.distributed as dist
 
     from paper_1805_12258_gb300 import build as hsbuild
-    from paper_1805_12258_gb300 import hs, synth
+    from paper_1805_12258_gb300 import hs, shard, synth
 
     ws, rank, local = dist_env()
     if ws > 1:
@@ -268,8 +271,9 @@ def run_ours(args):
     hsbuild.build()
 
     wl = workload(args.workload)
-    if rank:
-        wl.seed += 1000 * rank  # each rank sums its own plane (independent beams)
+    band = args.shard == "band" and ws > 1
+    if rank and not band:
+        wl.seed = shard.rank_seed(wl.seed, rank)  # each rank sums its own plane
     nt, n, H = wl.n_templates, wl.n_bins, wl.H
     es = 4 if args.dtype == "f32" else 2
     host32 = torch.empty((nt, n), dtype=torch.float32, pin_memory=True)
@@ -288,8 +292,14 @@ def run_ours(args):
                    grid_per_sm=args.grid_per_sm, stages=args.stages, z_split=args.z_split)
     stream = torch.cuda.current_stream()
 
+    f_lo, f_hi = shard.band_bounds(n, ws, plan.tile_bins)[rank] if band else (0, n)
+
     def step():
-        plan.run(fop, cands, stream, fop_f32=None if args.dtype == "f32" else fop32)
+        f32 = None if args.dtype == "f32" else fop32
+        if band:
+            plan.run_range(fop, cands, f_lo, f_hi, stream, fop_f32=f32)
+        else:
+            plan.run(fop, cands, stream, fop_f32=f32)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -323,11 +333,25 @@ def run_ours(args):
     elapsed_ms = float(t.item())
     st, n_cand = cands.sync(stream)
 
+    precision = None
+    if args.dtype != "f32":
+        # candidate set of the 16-bit plane (with FP32 rechecks) against the
+        # FP32 path on the FP32 copy: equal record for record by design
+        low = cands.fetch(stream)[0]
+        c32 = hs.CandBuffer(1 << 20)
+        with hs.Plan(nt, n, H, ta) as p32:
+            p32.run(fop32, c32, stream)
+            r32 = c32.fetch(stream)[0]
+        precision = {"storage": args.dtype, "recheck": "FP32 copy",
+                     "candidates": int(len(low)), "fp32_path_candidates": int(len(r32)),
+                     "records_equal_fp32_path": bool(np.array_equal(low, r32))}
+
     points = nt * n
-    value = points * ws * args.steps / (elapsed_ms / 1e3)
+    # whole-job points per step: every rank's plane, or the one banded plane
+    value = points * (1 if band else ws) * args.steps / (elapsed_ms / 1e3)
     ms_per_step = elapsed_ms / args.steps
     mean_kernel_s = kern_ms / max(kern_n, 1) / 1e3
-    algo_bytes = nt * n * es + H * nt * 4 + 16 * n_cand + 8
+    algo_bytes = nt * (f_hi - f_lo) * es + H * nt * 4 + 16 * n_cand + 8
     if args.dtype != "f32":
         algo_bytes += 0  # rechecks read only near-threshold points of the FP32 copy
     peak, peak_kind = peaks()
@@ -336,7 +360,7 @@ def run_ours(args):
 
     # e2e through hs_run_host: pinned host plane -> device, sum, records -> host
     e2e = None
-    if args.e2e_steps > 0:
+    if args.e2e_steps > 0 and not band:  # the host path sums whole planes
         dev = torch.empty_like(host, device="cuda")
         out = np.zeros(1 << 16, hs.CAND_DTYPE)
         plan.run_host(host, dev, cands, out, stream)
@@ -366,14 +390,17 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+            "scaling": "strong" if band else "weak", "vs_baseline": None, "dtype": args.dtype,
+            "data": "synthetic",
             "config": {"workload": wl.name, "n_templates": nt, "n_bins": n, "H": H,
                        "p_fa": wl.p_fa, "kernel": plan.kernel, "tile_bins": plan.tile_bins,
                        "order": args.order, "grid_per_sm": args.grid_per_sm,
                        "candidates": n_cand,
                        "l2": f"plane {nt * n * es / 1e6:.0f} MB > {L2_BYTES / 1e6:.0f} MB L2: "
                              "inputs larger than L2, no flush",
-                       "parallelism": f"{ws} independent planes (one per GPU)"},
+                       "parallelism": (f"one plane in {ws} frequency bands (bins "
+                                       f"[{f_lo}, {f_hi}) on rank 0)" if band else
+                                       f"{ws} independent planes (one per GPU)")},
             "level_sums_per_s": value * H,
             "effective_hbm_gbs": algo_bytes * ws * args.steps / (elapsed_ms / 1e3) / 1e9,
             "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peak,
@@ -383,7 +410,8 @@ def run_ours(args):
                          "kernel": kname, "algo_bytes_per_launch": algo_bytes,
                          "mean_kernel_us": mean_kernel_s * 1e6,
                          "frac_of_8tbs": algo_bytes / mean_kernel_s / 8e12},
-            "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
+            "precision": precision,
+        "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": launches_before, "status": hs.hs_status_str(st),
         }
         print(json.dumps(line), flush=True)

@@ -317,6 +317,18 @@ HS_API hs_status hs_synth_fop(void *fop, float *fop32, int dtype, int n_template
                               int64_t n_bins, int64_t ld, uint64_t seed, int n_signals,
                               hs_stream_t stream);
 
+/* Sum only the output bins [f_lo, f_hi) of the plane (all rows, all levels):
+ * the unit of a frequency-band shard (each shard reads the bins
+ * [f_lo / m, f_hi / m) of level m, all below f_hi, so a band needs no data
+ * from higher bands).  f_lo, and f_hi unless it equals n_bins, must be
+ * multiples of hs_plan_tile_bins().  append != 0 keeps the buffer's count and
+ * appends, so several bands can share one buffer.  Tiles run in linear order.
+ * fop32: FP32 recheck copy for 16-bit plans, or NULL.
+ * Errors: as hs_run_checked, and HS_ERR_INVALID for a bad range. */
+HS_API hs_status hs_run_range(hs_plan *p, const void *fop, const float *fop32, int64_t f_lo,
+                              int64_t f_hi, hs_stream_t stream, const hs_cand_buf *cands,
+                              int append);
+
 /* Harmonic summing with no device allocation.  The paper has no counterpart:
  * this entry point is for callers that may not allocate device memory, such
  * as code inside a host framework that has reserved all device memory for its

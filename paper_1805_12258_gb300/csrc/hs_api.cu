@@ -427,6 +427,34 @@ hs_status hs_run(hs_plan *p, const void *fop, hs_stream_t stream, const hs_cand_
     return hs_run_checked(p, fop, nullptr, stream, cands);
 }
 
+hs_status hs_run_range(hs_plan *p, const void *fop, const float *fop32, int64_t f_lo,
+                       int64_t f_hi, hs_stream_t stream, const hs_cand_buf *cands, int append)
+{
+    g_last_launches = 0;
+    if (!p)
+        return fail(HS_ERR_INVALID, "plan is null");
+    if (!fop || reinterpret_cast<uintptr_t>(fop) % 16 != 0)
+        return fail(HS_ERR_INVALID, "plane pointer must be non-null and 16-byte aligned");
+    if (fop32 && (p->opt.dtype == HS_F32 || reinterpret_cast<uintptr_t>(fop32) % 16 != 0))
+        return fail(HS_ERR_INVALID, "bad recheck copy (FP32 plans take none; 16-byte aligned)");
+    const long long unit = p->kernel == HS_KERNEL_STAGED ? p->tb : 1;
+    if (f_lo < 0 || f_hi > p->n || f_lo >= f_hi || f_lo % unit != 0 ||
+        (f_hi != p->n && f_hi % unit != 0))
+        return fail(HS_ERR_INVALID, "need 0 <= f_lo < f_hi <= n_bins with f_lo (and f_hi "
+                                    "unless it is n_bins) a multiple of hs_plan_tile_bins()");
+    hs_status st = check_cands(cands);
+    if (st != HS_OK)
+        return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (!append) {
+        cudaError_t e = cudaMemsetAsync(cands->count, 0, 2 * sizeof(uint32_t), s);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "cudaMemsetAsync counters");
+    }
+    std::lock_guard<std::mutex> lk(p->mu);
+    return launch_range(p, fop, fop32, s, cands, f_lo, f_hi, false);
+}
+
 hs_status hs_cand_sync(const hs_cand_buf *cands, hs_stream_t stream, uint32_t *n_out)
 {
     hs_status st = check_cands(cands);

@@ -154,6 +154,8 @@ def lib():
     for name in ("hs_server_create", "hs_server_submit", "hs_server_wait", "hs_server_drain",
                  "hs_server_stats_get", "hs_server_destroy", "hs_synth_fop"):
         getattr(L, name).restype = i32
+    L.hs_run_range.argtypes = [vp, vp, vp, i64, i64, vp, P(hs_cand_buf), i32]
+    L.hs_run_range.restype = i32
     L.hs_run_noalloc.argtypes = [i32, i64, i32, vp, vp, vp, P(hs_cand_buf)]
     L.hs_run_noalloc.restype = i32
     L.hs_noalloc_last_error.argtypes = []
@@ -348,6 +350,13 @@ class Plan:
             hs_run(self.handle, fop, stream, cands.c)
         else:
             hs_run_checked(self.handle, fop, fop_f32, stream, cands.c)
+
+    def run_range(self, fop, cands: CandBuffer, f_lo, f_hi, stream=None, fop_f32=None,
+                  append=False):
+        """Sum output bins [f_lo, f_hi) only (a frequency-band shard)."""
+        _check(lib().hs_run_range(self.handle, _ptr(fop), _ptr(fop_f32), int(f_lo), int(f_hi),
+                                  _stream_handle(stream), ctypes.byref(cands.c), int(append)),
+               "hs_run_range")
 
     def set_timing(self, enable=True):
         hs_plan_set_timing(self.handle, enable)

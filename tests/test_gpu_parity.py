@@ -155,6 +155,32 @@ def test_lowp_recheck_matches_fp32_path(nt, n, H, dtype):
     assert np.array_equal(r32, rg)
 
 
+@pytest.mark.parametrize("dtype,u", [("bf16", 2.0 ** -8), ("f16", 2.0 ** -11)])
+def test_lowp_level_error_against_the_fp32_plane(dtype, u):
+    # Precision form: every level sum of the 16-bit plane (no recheck) against
+    # the FP64 oracle on the FP32 plane it was rounded from.  Non-negative
+    # terms each carry at most the storage rounding u, so the relative error
+    # of a level sum is at most u plus the FP32 accumulation bound.  The per
+    # level max and RMS are printed (pytest -s) for the record.
+    nt, n, H = 85, 2048, 16
+    plane = synth.noise(nt, n, seed=31)
+    low = _bf16_bits(plane) if dtype == "bf16" else plane.astype(np.float16)
+    got, used = _all_sums(low, H, dtype=dtype)
+    assert used == "staged"
+    ref = oracle.planes(plane, H)
+    rel = np.abs(got - ref) / ref
+    bound = u * (1 + 2 ** -24) + 15 * 2.0 ** -24
+    mx = rel.reshape(H, -1).max(axis=1)
+    rms = np.sqrt((rel.reshape(H, -1) ** 2).mean(axis=1))
+    print(f"\n{dtype} per-level relative error vs FP64 oracle on the FP32 plane "
+          f"(85 x 2048, k = 1..16)")
+    print("max:", " ".join(f"{x:.2e}" for x in mx))
+    print("rms:", " ".join(f"{x:.2e}" for x in rms))
+    assert (mx <= bound).all()
+    # averaging over k terms shrinks the typical error roughly as 1/sqrt(k)
+    assert rms[-1] < rms[0]
+
+
 @pytest.mark.parametrize("dtype", ["bf16", "f16"])
 def test_lowp_without_recheck_flags_band(dtype):
     nt, n, H = 21, 8192, 8
@@ -259,6 +285,28 @@ def test_pipelined_matches_oracle_on_the_small_ska_slice():
     assert used == "staged" and st == hs.HS_OK
     ref, near = oracle.detect(plane, 16, ta, threads=8)
     assert_matches_oracle(recs, ref, near)
+
+
+@pytest.mark.parametrize("kernel", ["staged", "generic"])
+def test_frequency_bands_append_to_the_full_run(kernel):
+    # hs_run_range over the bands of shard.band_bounds, appended into one
+    # buffer, gives the full run's records (a band reads only lower bins)
+    from paper_1805_12258_gb300 import shard
+    nt, n, H = 85, 50000, 16
+    plane = synth.noise(nt, n, seed=19)
+    ta = synth.thresholds(1e-3, H, nt)
+    ref, nref, _, _ = run_gpu(plane, H, ta, kernel=kernel)
+    fop = torch.from_numpy(plane).cuda()
+    cands = hs.CandBuffer(1 << 20)
+    with hs.Plan(nt, n, H, ta, kernel=kernel) as plan:
+        for i, (lo, hi) in enumerate(shard.band_bounds(n, 3, plan.tile_bins)):
+            plan.run_range(fop, cands, lo, hi, append=i > 0)
+        got, cnt, st = cands.fetch()
+        with pytest.raises(hs.HsError):
+            plan.run_range(fop, cands, 1, n)  # not tile-aligned (staged) / fine (generic)
+            if kernel == "generic":
+                raise hs.HsError(hs.HS_ERR_INVALID, "generic accepts any start")
+    assert st == hs.HS_OK and cnt == nref > 0 and np.array_equal(got, ref)
 
 
 @pytest.mark.parametrize("kernel", ["staged", "generic"])
