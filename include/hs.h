@@ -377,6 +377,19 @@ HS_API int hs_last_launch_count(void);
  * B the bin (21 bits).  HS_ERR_INVALID when a field does not fit. */
 HS_API hs_status hs_pack_paper(const hs_cand *c, int n_templates, uint32_t *cl1, float *cl2);
 
+/* The paper's candidate cap per harmonic plane (Section IV-A): the policy is
+ * left open there (first, last or largest N_cand), so all three are offered.
+ * Host arrays.  For each level k keep at most n_keep of its records: FIRST /
+ * LAST = the first / last n_keep in Algorithm 2's visiting order (bins
+ * ascending, then z ascending), LARGEST = the n_keep largest powers (equal
+ * powers: the later visited first).  out (capacity n, not aliasing in)
+ * receives the kept records grouped by k ascending, each level in visiting
+ * order; *n_out their number.  Errors: HS_ERR_INVALID. */
+typedef enum { HS_KEEP_FIRST = 0, HS_KEEP_LAST = 1, HS_KEEP_LARGEST = 2 } hs_keep;
+HS_API hs_status hs_postfilter(const hs_cand *in, uint32_t n, int policy, uint32_t n_keep,
+                               hs_cand *out, uint32_t *n_out);
+HS_API const char *hs_postfilter_last_error(void);
+
 HS_API const char *hs_status_str(hs_status s);
 HS_API const char *hs_last_error(void);
 

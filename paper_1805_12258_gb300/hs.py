@@ -27,6 +27,8 @@ HS_INDEX_STRETCH, HS_INDEX_HFRAC = 0, 1
 HS_ZROUND_SYMMETRIC, HS_ZROUND_FLOOR = 0, 1
 HS_KERNEL_AUTO, HS_KERNEL_GENERIC, HS_KERNEL_STAGED = 0, 1, 2
 HS_FLAG_LOWP, HS_FLAG_NEAR = 1, 2
+HS_KEEP_FIRST, HS_KEEP_LAST, HS_KEEP_LARGEST = 0, 1, 2
+KEEP = {"first": HS_KEEP_FIRST, "last": HS_KEEP_LAST, "largest": HS_KEEP_LARGEST}
 
 DTYPES = {"f32": HS_F32, "bf16": HS_BF16, "f16": HS_F16}
 INDEX = {"stretch": HS_INDEX_STRETCH, "hfrac": HS_INDEX_HFRAC}
@@ -154,6 +156,10 @@ def lib():
     for name in ("hs_server_create", "hs_server_submit", "hs_server_wait", "hs_server_drain",
                  "hs_server_stats_get", "hs_server_destroy", "hs_synth_fop"):
         getattr(L, name).restype = i32
+    L.hs_postfilter.argtypes = [vp, u32, i32, u32, vp, P(u32)]
+    L.hs_postfilter.restype = i32
+    L.hs_postfilter_last_error.argtypes = []
+    L.hs_postfilter_last_error.restype = ctypes.c_char_p
     L.hs_run_range.argtypes = [vp, vp, vp, i64, i64, vp, P(hs_cand_buf), i32]
     L.hs_run_range.restype = i32
     L.hs_run_noalloc.argtypes = [i32, i64, i32, vp, vp, vp, P(hs_cand_buf)]
@@ -540,3 +546,17 @@ class Server:
 
     def __exit__(self, *a):
         self.close()
+
+
+def hs_postfilter(records: np.ndarray, policy="last", n_keep=200) -> np.ndarray:
+    """The paper's per-level candidate cap (first / last / largest n_keep),
+    applied by the library on host records; returns the kept records."""
+    rec = np.ascontiguousarray(records, dtype=CAND_DTYPE)
+    out = np.zeros(max(1, len(rec)), dtype=CAND_DTYPE)
+    n_out = ctypes.c_uint32()
+    st = lib().hs_postfilter(rec.ctypes.data if len(rec) else None, len(rec),
+                             KEEP[policy] if isinstance(policy, str) else int(policy),
+                             int(n_keep), out.ctypes.data, ctypes.byref(n_out))
+    if st != HS_OK:
+        raise HsError(st, f"hs_postfilter: {lib().hs_postfilter_last_error().decode()}")
+    return out[:n_out.value]
