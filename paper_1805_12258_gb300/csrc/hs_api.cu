@@ -106,6 +106,7 @@ int hs::group_bounds(const float *ta, int n_templates, int H, float delta, float
 {
     int ends[kMaxGroups];
     const int groups = staged_groups(H, ends);
+    double lowered[kMaxGroups], scale = 0.0;
     int a = 1;
     for (int g = 0; g < groups; ++g) {
         double t = INFINITY;
@@ -115,13 +116,24 @@ int hs::group_bounds(const float *ta, int n_templates, int H, float delta, float
         // A hit needs s (1 + delta) > t - band_abs; the fast pass sums a
         // group in tree order, within 2*gamma_H of the ascending sum, so
         // the bound is lowered by a further relative H*2^-22 (> 2 gamma_H)
-        double lowered = (t - band_abs) / (1.0 + delta);
-        lowered -= std::fabs(lowered) * H * std::ldexp(1.0, -22);
-        float lf = (float)lowered;
-        if ((double)lf > lowered)
+        lowered[g] = (t - band_abs) / (1.0 + delta);
+        lowered[g] -= std::fabs(lowered[g]) * H * std::ldexp(1.0, -22);
+        scale = std::max(scale, std::fabs(lowered[g]));
+        a = ends[g] + 1;
+    }
+    // The fast pass carries the bounds inside its sums (each group's first
+    // level holds bound_{g-1} - bound_g).  Near a bound every partial sum is
+    // at most about twice the largest bound in magnitude, and a pair's test
+    // takes fewer than 32 roundings, so an absolute 2^-16 of the largest bound
+    // (> 32 * 2^-24 * 2 * max|bound|) covers the mixing of signs; far from a
+    // bound the sign of d cannot change.
+    const double margin = std::ldexp(scale, -16) + std::ldexp(1.0, -126);
+    for (int g = 0; g < groups; ++g) {
+        const double v = lowered[g] - margin;
+        float lf = (float)v;
+        if ((double)lf > v)
             lf = std::nextafter(lf, -INFINITY);
         out[g] = lf;
-        a = ends[g] + 1;
     }
     return groups;
 }

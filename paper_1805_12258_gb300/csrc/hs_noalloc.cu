@@ -124,22 +124,8 @@ extern "C" hs_status hs_run_noalloc(int n_templates, int64_t n_bins, int H,
     const StagedShape sh{n_templates, H, tb, HS_F32};
     if (staged_available(sh) && (n_bins * 4) % 16 == 0) {
         // prefilter bounds per level group, as a plan computes them
-        int ends[kMaxGroups];
-        const int groups = staged_groups(H, ends);
         float tmin[kMaxGroups];
-        int a = 1;
-        for (int g = 0; g < groups; ++g) {
-            double t = INFINITY;
-            for (int k = a; k <= ends[g]; ++k)
-                for (int r = 0; r < n_templates; ++r)
-                    t = std::fmin(t, (double)thresholds[(size_t)(k - 1) * n_templates + r]);
-            double lowered = t - std::fabs(t) * H * std::ldexp(1.0, -22);
-            float lf = (float)lowered;
-            if ((double)lf > lowered)
-                lf = std::nextafter(lf, -INFINITY);
-            tmin[g] = lf;
-            a = ends[g] + 1;
-        }
+        group_bounds(thresholds, n_templates, H, 0.f, 0.f, tmin);
         auto fn = encode_fn();
         if (!fn)
             return fail(HS_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");

@@ -208,12 +208,26 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
     const bool ok = !any_of(!mbar_wait_bounded(bar, parity, kWaitLimitNs));
 
     // ---- fast pass: every row pair, group prefilter ------------------------------
-    // d = HP_b - bound has its sign bit set exactly when HP_b < bound (IEEE
-    // subtraction is sign-exact without flush-to-zero), so AND-ing the sign
-    // bits of every group's d leaves bit 31 set iff no group of the pair can
-    // hold a hit.
-    float2 ntg[C::G];
-    static_for<0, C::G>([&](auto g) { ntg[g] = make_float2(-p.tmin[g], -p.tmin[g]); });
+    // d_g = HP_b - bound_g (b the last level of group g) has its sign bit set
+    // exactly when HP_b < bound_g (IEEE addition is sign-exact without
+    // flush-to-zero), so AND-ing the sign bits of every group's d leaves bit
+    // 31 set iff no group of the pair can hold a hit.  The bounds ride along
+    // in the sums: the first level of group g carries c_g = bound_{g-1} -
+    // bound_g (c_0 = -bound_0) from the moment it is loaded, so the running
+    // sum over the groups is d_g itself and no separate subtraction is needed.
+    // The host lowers the bounds by the rounding this mixing of signs adds.
+    float2 cg[C::G];
+    static_for<0, C::G>([&](auto g) {
+        const float c = g == 0 ? -p.tmin[0] : p.tmin[g - 1] - p.tmin[g];
+        cg[g] = make_float2(c, c);
+    });
+    // the group whose first level is m, or -1
+    auto first_of = [](int m) {
+        for (int g = 0; g < C::G; ++g)
+            if (C::GLO(g) == m)
+                return g;
+        return -1;
+    };
     uint32_t negbits = 0u;
     uint64_t mask = 0ull;
     float2 cur[H];
@@ -227,16 +241,23 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
                 acc = gs;
             else
                 acc = __fadd2_rn(acc, gs);
-            const float2 d = __fadd2_rn(acc, ntg[g]);
-            sgn &= __float_as_uint(d.x) & __float_as_uint(d.y);
+            sgn &= __float_as_uint(acc.x) & __float_as_uint(acc.y);
         });
         return (~sgn) >> 31; // 1: the pair may hold a hit
+    };
+    // the value of level m at the pair (tv, bv), with its group's bound share
+    auto put = [&](auto M, float tv, float bv) {
+        constexpr int g = first_of(decltype(M)::value + 1);
+        if constexpr (g >= 0)
+            cur[M] = __fadd2_rn(make_float2(tv, bv), cg[g]);
+        else
+            cur[M] = make_float2(tv, bv);
     };
     if (ok) {
         // template z = 0: every stretch reads the centre row
         static_for<0, H>([&](auto M) {
             const float v = to_f32(sm[bidx[M]]);
-            cur[M] = make_float2(v, v);
+            put(M, v, v);
             negbits |= __float_as_uint(v);
         });
         mask = pair_test();
@@ -249,7 +270,7 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
                     constexpr int off = (zz / m) * C::W(m);
                     const float tv = to_f32(sm[bidx[M] + off]);
                     const float bv = to_f32(sm[bidx[M] - off]);
-                    cur[M] = make_float2(tv, bv);
+                    put(M, tv, bv);
                     negbits |= __float_as_uint(tv) | __float_as_uint(bv);
                 }
             });
