@@ -230,6 +230,13 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
     };
     uint32_t negbits = 0u;
     uint64_t mask = 0ull;
+    // How the pairs' outcomes are kept (measured choice per element type):
+    // 16-bit planes shift each pair's sign AND into clear[w] (one funnel
+    // shift per pair; set = no group can hit; pairs 0..31 in word 0, the rest
+    // in word 1) and convert once at the end; FP32 planes OR each outcome
+    // straight into the 64-bit mask.
+    constexpr bool kShiftIn = sizeof(T) == 2;
+    uint32_t clear[2] = {0u, 0u};
     float2 cur[H];
     auto pair_test = [&]() -> uint32_t {
         float2 acc = make_float2(0.f, 0.f);
@@ -243,7 +250,16 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
                 acc = __fadd2_rn(acc, gs);
             sgn &= __float_as_uint(acc.x) & __float_as_uint(acc.y);
         });
-        return (~sgn) >> 31; // 1: the pair may hold a hit
+        return sgn; // bit 31 clear: the pair may hold a hit
+    };
+    auto record = [&](auto ZZ, uint32_t sgn) {
+        constexpr int zz = decltype(ZZ)::value;
+        if constexpr (kShiftIn) {
+            constexpr int w = zz < 32 ? 0 : 1;
+            clear[w] = __funnelshift_l(sgn, clear[w], 1); // (clear << 1) | sgn >> 31
+        } else {
+            mask |= (uint64_t)((~sgn) >> 31) << zz;
+        }
     };
     // the value of level m at the pair (tv, bv), with its group's bound share
     auto put = [&](auto M, float tv, float bv) {
@@ -260,7 +276,7 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
             put(M, v, v);
             negbits |= __float_as_uint(v);
         });
-        mask = pair_test();
+        record(std::integral_constant<int, 0>{}, pair_test());
         // pairs (+zz, -zz): reload the value of m only when m divides zz
         static_for<1, Z + 1>([&](auto ZZ) {
             constexpr int zz = ZZ;
@@ -274,8 +290,19 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
                     negbits |= __float_as_uint(tv) | __float_as_uint(bv);
                 }
             });
-            mask |= (uint64_t)pair_test() << zz;
+            record(ZZ, pair_test());
         });
+        // word 0 holds pairs 0 .. n0-1 with pair zz at bit n0-1-zz, word 1
+        // pairs 32 .. Z with pair zz at bit Z-zz; reverse the bits into the
+        // mask (bit zz = the pair may hold a hit)
+        static_assert(Z <= 63, "two mask words");
+        if constexpr (kShiftIn) {
+            constexpr int n0 = Z + 1 < 32 ? Z + 1 : 32;
+            mask = (uint64_t)(__brev(~clear[0]) >> (32 - n0));
+            if constexpr (Z >= 32)
+                mask |= (uint64_t)((__brev(~clear[1]) >> (63 - Z)) & ((1u << (Z - 31)) - 1u))
+                        << 32;
+        }
     }
     if (!ok) {
         if (tid == 0)
