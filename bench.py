@@ -241,7 +241,7 @@ def run_reference(args):
         step()
     vals = [step() for _ in range(args.steps)]
     v = statistics.median(vals)
-    what = "the whole plane" if bins == n else f"bins [{lo}, {n})"
+    what = "all bins" if bins == n else f"bins [{lo}, {n})"
     sample = (f"all {nt} rows x {what} of the plane per step ({nt * bins} points, "
               f"{wl.H} levels, FP64), {cores} threads")
     print(json.dumps({
