@@ -291,6 +291,18 @@ def test_pipelined_matches_oracle_on_the_small_ska_slice():
     assert_matches_oracle(recs, ref, near)
 
 
+@pytest.mark.parametrize("n", [1 << 15, (1 << 15) + 128, 1 << 18])
+def test_tile_orders_give_the_same_records(n):
+    # the octave-interleaved order (the plan's tile table) visits every tile
+    # exactly once: the same records as the linear order
+    plane = synth.noise(85, n, seed=29)
+    ta = synth.thresholds(1e-4, 16, 85)
+    lin, nl, _, _ = run_gpu(plane, 16, ta, order=1)
+    oct_, no, st, used = run_gpu(plane, 16, ta, order=2)
+    assert used == "staged" and st == hs.HS_OK and nl == no > 0
+    assert np.array_equal(lin, oct_)
+
+
 @pytest.mark.parametrize("kernel", ["staged", "generic"])
 def test_frequency_bands_append_to_the_full_run(kernel):
     # hs_run_range over the bands of shard.band_bounds, appended into one
