@@ -151,18 +151,39 @@ __device__ __forceinline__ void group_sync(int id, int count)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
-// Wait for phase `parity` of the barrier for at most limit_ns nanoseconds.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
-                                                  uint64_t limit_ns)
+// One test of phase `parity` that may suspend the thread for up to hint_ns
+// until the phase completes (the hardware may return earlier).
+__device__ __forceinline__ bool mbar_try_wait_hint(uint32_t bar, uint32_t parity, uint32_t hint_ns)
 {
-    if (mbar_try_wait(bar, parity))
-        return true;
+    uint32_t done;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(done)
+                 : "r"(bar), "r"(parity), "r"(hint_ns)
+                 : "memory");
+    return done != 0u;
+}
+
+// The retry loop of mbar_wait_bounded, out of line so the waiting thread's
+// straight-line code carries no loop.
+static __device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, uint64_t limit_ns)
+{
     const uint64_t t0 = globaltimer_ns();
-    while (!mbar_try_wait(bar, parity)) {
+    while (!mbar_try_wait_hint(bar, parity, 100000u)) {
         if (globaltimer_ns() - t0 > limit_ns)
             return false;
     }
     return true;
+}
+
+// Wait for phase `parity` of the barrier for at most limit_ns nanoseconds.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
+                                                  uint64_t limit_ns)
+{
+    if (mbar_try_wait_hint(bar, parity, 1000000u)) // usually completes here
+        return true;
+    return mbar_wait_slow(bar, parity, limit_ns);
 }
 
 // 2-D tiled TMA load of one box into shared memory, completing on `bar`.
