@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"])
     ap.add_argument("--order", type=int, default=0)
     ap.add_argument("--tile-bins", type=int, default=0)
+    ap.add_argument("--index", default="stretch", choices=["stretch", "hfrac"],
+                    help="index map: the paper's stretch (Eq. 1-2) or harmonic fractions")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "staged", "generic"])
     ap.add_argument("--stages", type=int, default=0,
                     help="staged kernel: ring stages of the pipelined variant (0: one CTA per tile)")
     ap.add_argument("--z-split", type=int, default=0,
@@ -289,7 +292,8 @@ def run_ours(args):
     fop32 = fop if args.dtype == "f32" else host32.cuda()
     cands = hs.CandBuffer(1 << 20)
     plan = hs.Plan(nt, n, H, ta, dtype=args.dtype, order=args.order, tile_bins=args.tile_bins,
-                   grid_per_sm=args.grid_per_sm, stages=args.stages, z_split=args.z_split)
+                   grid_per_sm=args.grid_per_sm, stages=args.stages, z_split=args.z_split,
+                   index=args.index, kernel=args.kernel)
     stream = torch.cuda.current_stream()
 
     f_lo, f_hi = shard.band_bounds(n, ws, plan.tile_bins)[rank] if band else (0, n)
@@ -373,7 +377,8 @@ def run_ours(args):
         algo_bytes += 0  # rechecks read only near-threshold points of the FP32 copy
     peak, peak_kind = peaks()
     achieved_gbs = algo_bytes / mean_kernel_s / 1e9
-    kname = f"staged {nt}x{n} H={H} {args.dtype} tb={plan.tile_bins}"
+    kname = (f"staged {nt}x{n} H={H} {args.dtype} tb={plan.tile_bins}"
+             if plan.kernel == "staged" else f"generic {nt}x{n} H={H} {args.dtype} {args.index}")
 
     # e2e through hs_run_host: pinned host plane -> device, sum, records -> host
     e2e = None
@@ -410,7 +415,8 @@ def run_ours(args):
             "scaling": "strong" if band else "weak", "vs_baseline": None, "dtype": args.dtype,
             "data": "synthetic",
             "config": {"workload": wl.name, "n_templates": nt, "n_bins": n, "H": H,
-                       "p_fa": wl.p_fa, "kernel": plan.kernel, "tile_bins": plan.tile_bins,
+                       "p_fa": wl.p_fa, "kernel": plan.kernel, "index": args.index,
+                       "tile_bins": plan.tile_bins,
                        "order": args.order, "grid_per_sm": args.grid_per_sm,
                        "candidates": n_cand,
                        "l2": (f"plane {nt * n * es / 1e6:.1f} MB < {L2_BYTES / 1e6:.0f} MB L2: "
