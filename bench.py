@@ -385,14 +385,17 @@ def run_ours(args):
     if args.e2e_steps > 0 and not band:  # the host path sums whole planes
         dev = torch.empty_like(host, device="cuda")
         out = np.zeros(1 << 16, hs.CAND_DTYPE)
-        plan.run_host(host, dev, cands, out, stream)
+        # 16-bit planes: only the 16-bit plane crosses the host link in bulk;
+        # the rechecks read the page-locked FP32 copy in place
+        h32 = None if args.dtype == "f32" else host32
+        plan.run_host(host, dev, cands, out, stream, fop32_host=h32)
         torch.cuda.synchronize()
         if ws > 1:
             dist.barrier()
         t0 = time.perf_counter()
         d2h = 0
         for _ in range(args.e2e_steps):
-            _, ne = plan.run_host(host, dev, cands, out, stream)
+            _, ne = plan.run_host(host, dev, cands, out, stream, fop32_host=h32)
             d2h += 8 + 16 * min(ne, len(out))
         te = time.perf_counter() - t0
         tt = torch.tensor([te], device="cuda")
@@ -401,7 +404,10 @@ def run_ours(args):
         te = float(tt.item())
         e2e = {"value": points * ws * args.e2e_steps / te, "unit": UNIT,
                "h2d_bytes_per_step": nt * n * es, "d2h_bytes_per_step": d2h // args.e2e_steps,
-               "ms_per_step": te * 1e3 / args.e2e_steps}
+               "ms_per_step": te * 1e3 / args.e2e_steps,
+               "e2e_candidates_equal_device_run": bool(ne == n_cand)}
+        if h32 is not None:
+            e2e["recheck"] = "FP32 copy read in place from page-locked host memory"
         del dev
 
     cpu = None

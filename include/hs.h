@@ -163,6 +163,19 @@ HS_API hs_status hs_run_host(hs_plan *plan, const void *fop_host, void *fop_dev,
                       const hs_cand_buf *cands, hs_cand *host_records,
                       uint32_t host_capacity, hs_stream_t stream, uint32_t *n_out);
 
+/* As hs_run_host for a 16-bit plan whose FP32 copy stays in page-locked host
+ * memory: the few near-threshold points are re-added from fop32_host, read by
+ * the kernel across the host link, so only the 16-bit plane crosses it in
+ * bulk and the candidates equal the FP32 path's.  fop32_host: [n_templates]
+ * [row pitch] FP32 host memory the device can address (page-locked, or any
+ * host memory on systems with address translation), 16-byte aligned; NULL
+ * behaves as hs_run_host.  Errors as hs_run_host, and HS_ERR_INVALID for an
+ * FP32 plan or a copy the device cannot address. */
+HS_API hs_status hs_run_host_checked(hs_plan *plan, const void *fop_host, void *fop_dev,
+                                     const float *fop32_host, const hs_cand_buf *cands,
+                                     hs_cand *host_records, uint32_t host_capacity,
+                                     hs_stream_t stream, uint32_t *n_out);
+
 /* ---- Batched form: many planes (beams) of one shape -------------------------
  * The paper processes one plane per DM trial and several planes on separate
  * boards (Section VI-C); a pipeline has thousands per observation.  A batch

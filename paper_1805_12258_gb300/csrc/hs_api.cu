@@ -492,9 +492,33 @@ hs_status hs_run_host(hs_plan *p, const void *fop_host, void *fop_dev, const hs_
                       hs_cand *host_records, uint32_t host_capacity, hs_stream_t stream,
                       uint32_t *n_out)
 {
+    return hs_run_host_checked(p, fop_host, fop_dev, nullptr, cands, host_records, host_capacity,
+                               stream, n_out);
+}
+
+hs_status hs_run_host_checked(hs_plan *p, const void *fop_host, void *fop_dev,
+                              const float *fop32_host, const hs_cand_buf *cands,
+                              hs_cand *host_records, uint32_t host_capacity, hs_stream_t stream,
+                              uint32_t *n_out)
+{
     g_last_launches = 0;
     if (!p || !fop_host || !fop_dev)
         return fail(HS_ERR_INVALID, "plan, host plane and device plane must be non-null");
+    const float *fop32_dev = nullptr;
+    if (fop32_host) {
+        if (p->opt.dtype == HS_F32)
+            return fail(HS_ERR_INVALID, "an FP32 plan takes no recheck copy");
+        // rechecks read the few near-threshold points straight from the
+        // page-locked host copy (mapped into the device's address space)
+        void *dp = nullptr;
+        if (cudaHostGetDevicePointer(&dp, const_cast<float *>(fop32_host), 0) != cudaSuccess ||
+            reinterpret_cast<uintptr_t>(dp) % 16 != 0) {
+            cudaGetLastError();
+            return fail(HS_ERR_INVALID, "the FP32 recheck copy must be host memory the device "
+                                        "can address (page-locked), 16-byte aligned");
+        }
+        fop32_dev = static_cast<const float *>(dp);
+    }
     if (reinterpret_cast<uintptr_t>(fop_dev) % 16 != 0)
         return fail(HS_ERR_INVALID, "device plane must be 16-byte aligned");
     if (host_capacity > 0 && !host_records)
@@ -546,7 +570,7 @@ hs_status hs_run_host(hs_plan *p, const void *fop_host, void *fop_dev, const hs_
                 e = cudaStreamWaitEvent(s, p->chunk_events[c], 0);
             if (e != cudaSuccess)
                 return cuda_fail(e, "host-to-device chunk copy");
-            st = launch_range(p, fop_dev, nullptr, s, cands, prev, hi, false);
+            st = launch_range(p, fop_dev, fop32_dev, s, cands, prev, hi, false);
             if (st != HS_OK)
                 return st;
             prev = hi;

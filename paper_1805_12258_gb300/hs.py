@@ -123,6 +123,8 @@ def lib():
     L.hs_run_checked.argtypes = [vp, vp, vp, vp, P(hs_cand_buf)]
     L.hs_cand_sync.argtypes = [P(hs_cand_buf), vp, P(u32)]
     L.hs_run_host.argtypes = [vp, vp, vp, P(hs_cand_buf), vp, u32, vp, P(u32)]
+    L.hs_run_host_checked.argtypes = [vp, vp, vp, vp, P(hs_cand_buf), vp, u32, vp, P(u32)]
+    L.hs_run_host_checked.restype = i32
     L.hs_plan_destroy.argtypes = [vp]
     L.hs_plan_kernel.argtypes = [vp]
     L.hs_plan_tile_bins.argtypes = [vp]
@@ -237,14 +239,16 @@ def hs_cand_sync(cands: hs_cand_buf, stream):
     return st, n.value
 
 
-def hs_run_host(plan, fop_host, fop_dev, cands: hs_cand_buf, host_records, stream):
-    """Returns (status, n_found); host_records is a CAND_DTYPE numpy array."""
+def hs_run_host(plan, fop_host, fop_dev, cands: hs_cand_buf, host_records, stream,
+                fop32_host=None):
+    """Returns (status, n_found); host_records is a CAND_DTYPE numpy array.
+    fop32_host: page-locked FP32 copy for the rechecks of a 16-bit plan."""
     n = ctypes.c_uint32(0)
     cap = 0 if host_records is None else len(host_records)
-    st = lib().hs_run_host(plan, _ptr(fop_host), _ptr(fop_dev), ctypes.byref(cands),
-                           _ptr(host_records) if cap else None, cap, _stream_handle(stream),
-                           ctypes.byref(n))
-    _check(st, "hs_run_host", ok=(HS_OK, HS_ERR_OVERFLOW))
+    st = lib().hs_run_host_checked(plan, _ptr(fop_host), _ptr(fop_dev), _ptr(fop32_host),
+                                   ctypes.byref(cands), _ptr(host_records) if cap else None,
+                                   cap, _stream_handle(stream), ctypes.byref(n))
+    _check(st, "hs_run_host_checked", ok=(HS_OK, HS_ERR_OVERFLOW))
     return st, n.value
 
 
@@ -371,8 +375,10 @@ class Plan:
         """(summed kernel ms, launches) recorded since the last call."""
         return hs_plan_kernel_time(self.handle)
 
-    def run_host(self, fop_host, fop_dev, cands: CandBuffer, host_records, stream=None):
-        return hs_run_host(self.handle, fop_host, fop_dev, cands.c, host_records, stream)
+    def run_host(self, fop_host, fop_dev, cands: CandBuffer, host_records, stream=None,
+                 fop32_host=None):
+        return hs_run_host(self.handle, fop_host, fop_dev, cands.c, host_records, stream,
+                           fop32_host)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -186,6 +186,35 @@ def test_lowp_level_error_against_the_fp32_plane(dtype, u):
 
 
 @pytest.mark.parametrize("dtype", ["bf16", "f16"])
+def test_lowp_end_to_end_with_host_recheck_copy(dtype):
+    # hs_run_host_checked: the 16-bit plane is copied to the device in
+    # chunks, the FP32 copy stays in page-locked host memory and is read in
+    # place for rechecks; the records equal the FP32 path's
+    nt, n, H = 85, 1 << 15, 16
+    plane = synth.noise(nt, n, seed=37)
+    ta = synth.thresholds(1e-4, H, nt)
+    r32, n32, _, _ = run_gpu(plane, H, ta)
+    tdt = torch.bfloat16 if dtype == "bf16" else torch.float16
+    host32 = torch.from_numpy(plane).pin_memory()
+    host = host32.to(tdt).pin_memory()
+    dev = torch.empty_like(host, device="cuda")
+    cands = hs.CandBuffer(1 << 18)
+    out = np.zeros(1 << 18, hs.CAND_DTYPE)
+    with hs.Plan(nt, n, H, ta, dtype=dtype) as plan:
+        st, cnt = plan.run_host(host, dev, cands, out, fop32_host=host32)
+        assert st == hs.HS_OK and cnt == n32 > 0
+        assert np.array_equal(hs.sort_records(out[:cnt]), r32)
+        # pageable host memory: refused where the device cannot address it,
+        # read in place where it can (address translation); never wrong
+        try:
+            st2, cnt2 = plan.run_host(host, dev, cands, out, fop32_host=plane)
+        except hs.HsError as e:
+            assert e.status == hs.HS_ERR_INVALID
+        else:
+            assert st2 == hs.HS_OK and np.array_equal(hs.sort_records(out[:cnt2]), r32)
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
 def test_lowp_without_recheck_flags_band(dtype):
     nt, n, H = 21, 8192, 8
     plane = synth.noise(nt, n, seed=8)
