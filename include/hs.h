@@ -261,6 +261,14 @@ typedef struct {
     int64_t n_bins;           /* 1..slot_bins */
     int dtype;                /* HS_F32 or HS_BF16 */
     int n_signals;            /* injected signals, 0..16 */
+    /* A plane already resident in device memory (made upstream): when fop is
+     * not NULL the engine sums it in place instead of generating one into the
+     * slot (seed and n_signals unused).  Borrowed until the request is done;
+     * 16-byte aligned rows of pitch ld (0 = n_bins; ld * element size a
+     * multiple of 16).  BF16 planes need their FP32 copy fop32 (same pitch). */
+    const void *fop;
+    const float *fop32;
+    int64_t ld;
 } hs_request;
 
 typedef struct {

@@ -286,15 +286,31 @@ void launch_group(hs_server *s, Group &g)
     for (const Req &r : g.reqs) {
         const long long n = r.r.n_bins;
         const bool lowp = r.r.dtype == HS_BF16;
-        float *f32 = s->d_f32 + slot_elems * r.slot;
-        __nv_bfloat16 *bf = s->d_bf + slot_elems * r.slot;
-        if (st == HS_OK)
-            st = synth(lowp ? (void *)bf : (void *)f32, lowp ? f32 : nullptr, r.r.dtype, nt, n,
-                       s->ld_max, r.r.seed, r.r.n_signals, st_, false);
-        StagedBatchBeam d = s->slot_beam[lowp ? 1 : 0][(size_t)r.slot];
-        d.fop32 = lowp ? f32 : nullptr;
+        StagedBatchBeam d;
+        if (r.r.fop) { // resident plane: descriptors for the caller's memory
+            std::memset(&d, 0, sizeof d);
+            const long long ld = r.r.ld ? r.r.ld : n;
+            const StagedShape sh{nt, s->cfg.H, 128, r.r.dtype};
+            for (int m = 1; m <= s->cfg.H && st == HS_OK; ++m) {
+                int w = 0, rows = 0;
+                staged_box(sh, m, &w, &rows);
+                if (encode_tensor_map(&d.maps[m - 1], r.r.dtype, r.r.fop, n, ld, nt, w, rows) !=
+                    CUDA_SUCCESS)
+                    st = fail(HS_ERR_CUDA, "cuTensorMapEncodeTiled failed for a resident plane");
+            }
+            d.fop32 = lowp ? r.r.fop32 : nullptr;
+            d.ld = ld;
+        } else {
+            float *f32 = s->d_f32 + slot_elems * r.slot;
+            __nv_bfloat16 *bf = s->d_bf + slot_elems * r.slot;
+            if (st == HS_OK)
+                st = synth(lowp ? (void *)bf : (void *)f32, lowp ? f32 : nullptr, r.r.dtype, nt,
+                           n, s->ld_max, r.r.seed, r.r.n_signals, st_, false);
+            d = s->slot_beam[lowp ? 1 : 0][(size_t)r.slot];
+            d.fop32 = lowp ? f32 : nullptr;
+            d.ld = s->ld_max;
+        }
         d.n = n;
-        d.ld = s->ld_max;
         d.rec = slot_records(s->d_out, s->out_stride, r.slot);
         d.counters = slot_counters(s->d_out, s->out_stride, r.slot);
         d.cap = cap;
@@ -570,6 +586,16 @@ hs_status hs_server_submit(hs_server *s, const hs_request *r, uint64_t *ticket)
         r->dtype != HS_BF16) || r->n_signals < 0 || r->n_signals > kMaxSignals)
         return fail(HS_ERR_INVALID, "request needs 1 <= n_bins <= slot_bins, dtype FP32 or "
                                     "BF16 and 0..16 signals");
+    if (r->fop) {
+        const long long ld = r->ld ? r->ld : r->n_bins;
+        const long long es = r->dtype == HS_F32 ? 4 : 2;
+        if (reinterpret_cast<uintptr_t>(r->fop) % 16 != 0 || ld < r->n_bins ||
+            (ld * es) % 16 != 0 ||
+            (r->dtype == HS_BF16 &&
+             (!r->fop32 || reinterpret_cast<uintptr_t>(r->fop32) % 16 != 0 || (ld * 4) % 16 != 0)))
+            return fail(HS_ERR_INVALID, "resident plane: 16-byte aligned rows of pitch ld >= "
+                                        "n_bins, and a BF16 plane's FP32 copy");
+    }
     std::lock_guard<std::mutex> lk(s->mu);
     s->st.submitted++;
     // requests beyond the free slots wait; at most queue_limit of them

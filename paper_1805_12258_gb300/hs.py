@@ -78,7 +78,8 @@ class hs_server_config(ctypes.Structure):
 
 class hs_request(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("n_bins", ctypes.c_int64), ("dtype", ctypes.c_int),
-                ("n_signals", ctypes.c_int)]
+                ("n_signals", ctypes.c_int), ("fop", ctypes.c_void_p), ("fop32", ctypes.c_void_p),
+                ("ld", ctypes.c_int64)]
 
 
 class hs_result(ctypes.Structure):
@@ -502,9 +503,13 @@ class Server:
         self.handle = out.value
         self.n_templates, self.H, self.cand_capacity = n_templates, H, int(cand_capacity)
 
-    def submit(self, seed, n_bins, dtype="f32", n_signals=0):
-        """Queue a request; returns its ticket, or None when the queue is full."""
-        req = hs_request(int(seed), int(n_bins), DTYPES[dtype], int(n_signals))
+    def submit(self, seed, n_bins, dtype="f32", n_signals=0, fop=None, fop32=None):
+        """Queue a request; returns its ticket, or None when the queue is full.
+        fop (and fop32 for BF16): a device plane already resident, summed in
+        place instead of generating one from the seed."""
+        ld = 0 if fop is None else int(fop.shape[-1])
+        req = hs_request(int(seed), int(n_bins), DTYPES[dtype], int(n_signals), _ptr(fop),
+                         _ptr(fop32), ld)
         t = ctypes.c_uint64()
         st = lib().hs_server_submit(self.handle, ctypes.byref(req), ctypes.byref(t))
         if st == HS_ERR_BUSY:

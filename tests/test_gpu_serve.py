@@ -149,6 +149,32 @@ def test_alone_equals_in_mix():
     assert max(r[0]["group_size"] for r in results.values()) > 1  # groups did form
 
 
+def test_resident_planes_are_summed_in_place():
+    # requests that bring a plane already in device memory (made upstream),
+    # FP32 and BF16 with its FP32 copy, mixed with generated ones: each gives
+    # the records of an hs_run of its plane
+    ta = synth.thresholds(1e-5, H, NT)
+    planes = []
+    for i, (n, dt) in enumerate([(70001, "f32"), (50000, "bf16"), (123457, "f32")]):
+        f32, bf = _plane(300 + i, n, dt, n_signals=4)
+        planes.append((n, dt, f32, bf))
+    with hs.Server(NT, H, ta, n_slots=4, slot_bins=1 << 17, cand_capacity=1 << 14) as srv:
+        tickets = []
+        for i, (n, dt, f32, bf) in enumerate(planes):
+            tickets.append(srv.submit(0, n, dt, 0, fop=f32 if dt == "f32" else bf,
+                                      fop32=None if dt == "f32" else f32))
+            tickets.append(srv.submit(900 + i, 40000, "bf16", 3))  # generated, in the mix
+        results = [srv.wait(t, 60000) for t in tickets]
+    for (n, dt, f32, bf), (res, got) in zip(planes, results[0::2]):
+        assert res["status"] == hs.HS_OK
+        cands = hs.CandBuffer(1 << 14)
+        with hs.Plan(NT, n, H, ta, row_pitch=f32.shape[1]) as plan:
+            plan.run(f32, cands)
+            ref, cnt, st = cands.fetch()
+        assert np.array_equal(got, ref) and len(ref) > 0
+    assert all(r[0]["status"] == hs.HS_OK for r in results[1::2])
+
+
 def test_admission_answers_busy_when_the_queue_is_full():
     ta = synth.thresholds(1e-8, H, NT)
     with hs.Server(NT, H, ta, n_slots=1, slot_bins=1 << 20, cand_capacity=256,
