@@ -360,7 +360,7 @@ def run_ours(args):
         # FP32 path on the FP32 copy: equal record for record by design
         low = cands.fetch(stream)[0]
         c32 = hs.CandBuffer(1 << 20)
-        with hs.Plan(nt, n, H, ta) as p32:
+        with hs.Plan(nt, n, H, ta, index=args.index, kernel=args.kernel) as p32:
             p32.run(fop32, c32, stream)
             r32 = c32.fetch(stream)[0]
         precision = {"storage": args.dtype, "recheck": "FP32 copy",

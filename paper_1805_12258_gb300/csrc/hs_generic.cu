@@ -146,6 +146,133 @@ __global__ void __launch_bounds__(128)
     }
 }
 
+// Level k of point (z, f) from the FP32 copy, out of line: the rechecks of
+// 16-bit planes are rare and stay off the fixed kernel's registers.
+__device__ __noinline__ float recheck_level(const float *fop32, int Z, long long ld, int index,
+                                            int zround, int z, unsigned f, int k)
+{
+    float a;
+    return level_value(fop32, Z, ld, index, zround, z, (long long)f, k, &a);
+}
+
+// The same computation for a level count fixed at compile time: every row
+// scale z h / k and bin scale f h / k becomes a division by a constant (a
+// multiply-high) instead of a runtime integer division, and the level values
+// stay in registers for the record pass.  Bins are 32-bit: the launcher uses
+// it when f h fits (f < 2^31 / H).
+template <int NUM, int DEN, int ZR>
+__device__ __forceinline__ int scale_row_c(int z)
+{
+    const int p = z * NUM;
+    if (ZR == HS_ZROUND_FLOOR) {
+        int q = p / DEN;
+        if ((p % DEN) != 0 && p < 0)
+            q -= 1;
+        return q;
+    }
+    return p >= 0 ? p / DEN : -((-p) / DEN);
+}
+
+template <typename T, int H, int INDEX, int ZR>
+__global__ void __launch_bounds__(128, 4)
+    generic_fixed_kernel(GenericArgs a, int rows_per_block)
+{
+    const T *fop = static_cast<const T *>(a.fop);
+    const int Z = (a.nt - 1) / 2;
+    const long long f64 = a.f_lo + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = f64 < a.f_hi;
+    const unsigned f = (unsigned)(valid ? f64 : a.f_lo);
+    const int z_lo = -Z + (int)blockIdx.y * rows_per_block;
+    const int z_hi = min(Z, z_lo + rows_per_block - 1);
+    auto ld = [&](int row, unsigned bin) {
+        return to_f32(__ldg(fop + (long long)row * a.ld + bin));
+    };
+
+    for (int z = z_lo; z <= z_hi; ++z) { // uniform over the block
+        const int row = z + Z;
+        float lv[H], la[H];
+        if constexpr (INDEX == HS_INDEX_STRETCH) {
+            float s = 0.f, ab = 0.f;
+            static_for<1, H + 1>([&](auto M) {
+                constexpr int m = M;
+                const float v = ld(scale_row_c<1, m, ZR>(z) + Z, f / (unsigned)m);
+                s = (m == 1) ? v : s + v;
+                ab += fabsf(v);
+                lv[m - 1] = s;
+                la[m - 1] = ab;
+            });
+        } else {
+            static_for<1, H + 1>([&](auto K) {
+                constexpr int k = K;
+                float s = 0.f, ab = 0.f;
+                static_for<1, k + 1>([&](auto Hh) {
+                    constexpr int h = Hh;
+                    const float v = ld(scale_row_c<h, k, ZR>(z) + Z, (f * (unsigned)h) / (unsigned)k);
+                    s = (h == 1) ? v : s + v;
+                    ab += fabsf(v);
+                });
+                lv[k - 1] = s;
+                la[k - 1] = ab;
+            });
+        }
+        // pass 1: hit mask over the levels; 16-bit planes re-add a possible
+        // hit from the FP32 copy (rare, out of line)
+        uint32_t hits = 0u;
+        static_for<0, H>([&](auto Kk) {
+            constexpr int k = Kk + 1;
+            const float thr = __ldg(a.ta + (k - 1) * a.nt + row);
+            bool hit;
+            if (a.delta == 0.f || a.fop32 == nullptr) {
+                hit = lv[Kk] > thr;
+            } else {
+                const float band = a.delta * la[Kk] + a.band_abs;
+                hit = !(lv[Kk] == lv[Kk] && lv[Kk] + band < thr) &&
+                      recheck_level(a.fop32, Z, a.ld, a.index, a.zround, z, f, k) > thr;
+            }
+            if (hit)
+                hits |= 1u << Kk;
+        });
+        if (!valid)
+            hits = 0u;
+        uint32_t slot = warp_reserve(a.counters, (uint32_t)__popc(hits));
+        // pass 2: the records of the hit levels
+        static_for<0, H>([&](auto Kk) {
+            constexpr int k = Kk + 1;
+            if (hits & (1u << Kk)) {
+                float power = lv[Kk];
+                uint32_t flags = 0u;
+                if (a.delta != 0.f) {
+                    if (a.fop32 != nullptr) {
+                        power = recheck_level(a.fop32, Z, a.ld, a.index, a.zround, z, f, k);
+                    } else {
+                        const float thr = __ldg(a.ta + (k - 1) * a.nt + row);
+                        flags = HS_FLAG_LOWP | (fabsf(lv[Kk] - thr) <= a.delta * la[Kk] + a.band_abs
+                                                    ? HS_FLAG_NEAR
+                                                    : 0u);
+                    }
+                }
+                put_record(a.rec, slot++, a.cap, f, z, k, flags, power);
+            }
+        });
+    }
+}
+
+template <typename T, int H>
+void launch_fixed(const GenericArgs &a, dim3 grid, int threads, int rows, cudaStream_t s)
+{
+    if (a.index == HS_INDEX_STRETCH) {
+        if (a.zround == HS_ZROUND_FLOOR)
+            generic_fixed_kernel<T, H, HS_INDEX_STRETCH, HS_ZROUND_FLOOR><<<grid, threads, 0, s>>>(a, rows);
+        else
+            generic_fixed_kernel<T, H, HS_INDEX_STRETCH, HS_ZROUND_SYMMETRIC><<<grid, threads, 0, s>>>(a, rows);
+    } else {
+        if (a.zround == HS_ZROUND_FLOOR)
+            generic_fixed_kernel<T, H, HS_INDEX_HFRAC, HS_ZROUND_FLOOR><<<grid, threads, 0, s>>>(a, rows);
+        else
+            generic_fixed_kernel<T, H, HS_INDEX_HFRAC, HS_ZROUND_SYMMETRIC><<<grid, threads, 0, s>>>(a, rows);
+    }
+}
+
 } // namespace
 
 cudaError_t launch_generic(const GenericArgs &a, cudaStream_t s)
@@ -165,6 +292,26 @@ cudaError_t launch_generic(const GenericArgs &a, cudaStream_t s)
     }
     const int by = (a.nt + rows_per_block - 1) / rows_per_block;
     dim3 grid((unsigned)bx, (unsigned)by);
+    // compiled level counts with 32-bit bin products take the fixed kernel
+    if ((a.H == 8 || a.H == 16) && a.f_hi <= (1LL << 31) / a.H) {
+        switch (a.dtype) {
+        case HS_F32:
+            a.H == 8 ? launch_fixed<float, 8>(a, grid, threads, rows_per_block, s)
+                     : launch_fixed<float, 16>(a, grid, threads, rows_per_block, s);
+            break;
+        case HS_BF16:
+            a.H == 8 ? launch_fixed<__nv_bfloat16, 8>(a, grid, threads, rows_per_block, s)
+                     : launch_fixed<__nv_bfloat16, 16>(a, grid, threads, rows_per_block, s);
+            break;
+        case HS_F16:
+            a.H == 8 ? launch_fixed<__half, 8>(a, grid, threads, rows_per_block, s)
+                     : launch_fixed<__half, 16>(a, grid, threads, rows_per_block, s);
+            break;
+        default:
+            return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     switch (a.dtype) {
     case HS_F32:
         generic_kernel<float><<<grid, threads, 0, s>>>(a, rows_per_block);
