@@ -393,6 +393,15 @@ HS_API hs_status hs_plan_kernel_time(hs_plan *plan, double *total_ms, int *launc
 /* Kernels launched by the last hs_run* call on this thread. */
 HS_API int hs_last_launch_count(void);
 
+/* Self-test of the bounded device waits (failure detection without a GPU
+ * fault): one CTA waits on an mbarrier phase that nothing completes, gives up
+ * after limit_ns (1 ns .. 10 s) and writes HS_ERR_TIMEOUT into counters[1]
+ * (device memory, the status word of an hs_cand_buf), as a summing kernel
+ * does when a tile's copies never arrive.  Asynchronous on `stream`; read the
+ * status with hs_cand_sync.  Errors: HS_ERR_INVALID, HS_ERR_CUDA. */
+HS_API hs_status hs_selftest_wait_timeout(uint32_t *counters, uint64_t limit_ns,
+                                          hs_stream_t stream);
+
 /* The paper's packed candidate form (Section III): CL1 = F*2^24 + H*2^21 + B,
  * CL2 = A, with F the row r = z + Z (7 bits), H the 0-based level (3 bits),
  * B the bin (21 bits).  HS_ERR_INVALID when a field does not fit. */

@@ -163,6 +163,8 @@ def lib():
     L.hs_postfilter.restype = i32
     L.hs_postfilter_last_error.argtypes = []
     L.hs_postfilter_last_error.restype = ctypes.c_char_p
+    L.hs_selftest_wait_timeout.argtypes = [vp, ctypes.c_uint64, vp]
+    L.hs_selftest_wait_timeout.restype = i32
     L.hs_run_range.argtypes = [vp, vp, vp, i64, i64, vp, P(hs_cand_buf), i32]
     L.hs_run_range.restype = i32
     L.hs_run_noalloc.argtypes = [i32, i64, i32, vp, vp, vp, P(hs_cand_buf)]

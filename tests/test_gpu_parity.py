@@ -5,6 +5,8 @@ rounding bound of at most 15 ascending additions of non-negative terms is
 below 9e-7); candidate sets identical except for points the oracle lists
 within 1e-5 relative of their threshold.
 """
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -352,6 +354,26 @@ def test_frequency_bands_append_to_the_full_run(kernel):
             if kernel == "generic":
                 raise hs.HsError(hs.HS_ERR_INVALID, "generic accepts any start")
     assert st == hs.HS_OK and cnt == nref > 0 and np.array_equal(got, ref)
+
+
+def test_a_wait_that_runs_out_reports_timeout_and_the_context_stays_usable():
+    # failure detection without a fault: a device wait on a barrier nothing
+    # completes gives up after 20 ms and reports HS_ERR_TIMEOUT; the next
+    # run on the same context is unaffected
+    cands = hs.CandBuffer(16)
+    cands.counters.zero_()
+    st = hs.lib().hs_selftest_wait_timeout(ctypes.c_void_p(cands.counters.data_ptr()),
+                                          20_000_000, hs._stream_handle(None))
+    assert st == hs.HS_OK
+    with pytest.raises(hs.HsError) as e:
+        cands.sync()
+    assert e.value.status == hs.HS_ERR_TIMEOUT
+    plane = synth.noise(21, 4096, seed=2)
+    ta = synth.thresholds(1e-3, 8, 21)
+    recs, cnt, st2, used = run_gpu(plane, 8, ta)
+    ref, near = oracle.detect(plane, 8, ta)
+    assert st2 == hs.HS_OK and used == "staged"
+    assert_matches_oracle(recs, ref, near)
 
 
 @pytest.mark.parametrize("kernel", ["staged", "generic"])
