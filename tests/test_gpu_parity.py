@@ -102,13 +102,16 @@ def test_every_level_sum(nt, n, H, kernel):
     np.testing.assert_allclose(got, ref, rtol=RTOL, atol=0)
 
 
+@pytest.mark.parametrize("nt,n,H", [(21, 777, 8), (85, 1000, 16), (33, 500, 13)])
 @pytest.mark.parametrize("index,zround", [("hfrac", "symmetric"), ("stretch", "floor"),
                                           ("hfrac", "floor")])
-def test_other_index_maps(index, zround):
-    plane = synth.noise(21, 777, seed=5)
-    got, used = _all_sums(plane, 8, index=index, zround=zround)
+def test_other_index_maps(index, zround, nt, n, H):
+    # H = 8 and 16 run the generic kernel's compile-time variant (harmonic
+    # fractions grouped into families that share loads), H = 13 the runtime one
+    plane = synth.noise(nt, n, seed=5)
+    got, used = _all_sums(plane, H, index=index, zround=zround)
     assert used == "generic"
-    ref = oracle.planes(plane, 8, index=oracle.HFRAC if index == "hfrac" else oracle.STRETCH,
+    ref = oracle.planes(plane, H, index=oracle.HFRAC if index == "hfrac" else oracle.STRETCH,
                         zround=oracle.ZFLOOR if zround == "floor" else oracle.ZSYM)
     np.testing.assert_allclose(got, ref, rtol=RTOL, atol=0)
 
