@@ -54,7 +54,9 @@ def parse():
                     help="serve workload: length of the Poisson arrival phase")
     ap.add_argument("--serve-rate", type=float, default=1000.0, help="arrivals per second")
     ap.add_argument("--slots", type=int, default=16, help="serve workload: resident slots")
-    ap.add_argument("--grid-per-sm", type=int, default=0)
+    ap.add_argument("--grid-per-sm", type=int, default=None,
+                    help="resident CTAs per SM walking tiles (0: one CTA per tile); the batch "
+                         "workload asks the autotuner when this is not given")
     ap.add_argument("--beams", type=int, default=64)
     ap.add_argument("--beam-log2", default="18,22",
                     help="batch workload: beam lengths log-uniform in [2^lo, 2^hi] bins")
@@ -292,7 +294,7 @@ def run_ours(args):
     fop32 = fop if args.dtype == "f32" else host32.cuda()
     cands = hs.CandBuffer(1 << 20)
     plan = hs.Plan(nt, n, H, ta, dtype=args.dtype, order=args.order, tile_bins=args.tile_bins,
-                   grid_per_sm=args.grid_per_sm, stages=args.stages, z_split=args.z_split,
+                   grid_per_sm=args.grid_per_sm or 0, stages=args.stages, z_split=args.z_split,
                    index=args.index, kernel=args.kernel)
     stream = torch.cuda.current_stream()
 
@@ -423,7 +425,7 @@ def run_ours(args):
             "config": {"workload": wl.name, "n_templates": nt, "n_bins": n, "H": H,
                        "p_fa": wl.p_fa, "kernel": plan.kernel, "index": args.index,
                        "tile_bins": plan.tile_bins,
-                       "order": args.order, "grid_per_sm": args.grid_per_sm,
+                       "order": args.order, "grid_per_sm": args.grid_per_sm or 0,
                        "candidates": n_cand,
                        "l2": (f"plane {nt * n * es / 1e6:.1f} MB < {L2_BYTES / 1e6:.0f} MB L2: "
                               "512 MB scratch written before every launch (cold); time = the "
@@ -478,14 +480,14 @@ def run_batch(args):
         dev = torch.empty((nt, ld), device="cuda").exponential_(generator=g)
         beams.append((dev, n, hs.CandBuffer(1 << 16)))
     points = nt * sum(sizes)
-    gps = args.grid_per_sm
+    gps, order = args.grid_per_sm, args.order
     tuned = None
-    if gps < 0:  # let the autotuner choose
+    if gps is None or gps < 0:  # the autotuner chooses tile order and grid
         best, table = autotune.tune_batch(nt, H, ta, beams)
-        gps = best["grid_per_sm"]
+        gps, order = best["grid_per_sm"], best.get("order", args.order)
         tuned = table
     stream = torch.cuda.current_stream()
-    with hs.Batch(nt, H, ta, grid_per_sm=gps, max_beams=len(beams), order=args.order) as batch:
+    with hs.Batch(nt, H, ta, grid_per_sm=gps, max_beams=len(beams), order=order) as batch:
         batch.set_beams(beams)
         for _ in range(max(3, args.warmup)):
             batch.graph_run(stream)
@@ -535,7 +537,7 @@ def run_batch(args):
                                f"log-uniform in [2^{lo:g}, 2^{hi:g}], H=16 fp32",
                    "beams": len(beams), "bins_total": sum(sizes), "tiles": tiles,
                    "launches_per_step": 1 + launches,
-                   "tile_order": "linear" if args.order == 1 else "octave-interleaved",
+                   "tile_order": "linear" if order == 1 else "octave-interleaved",
                    "grid_per_sm": gps, "graph": True, "candidates": n_cand,
                    "l2": "inputs larger than L2, no flush"},
         "sequential_hs_run_ms": t_seq, "batch_speedup_vs_sequential": t_seq / ms,

@@ -1,5 +1,7 @@
-"""Autotuner for the staged kernel: tile width, tile order and resident CTAs
-per SM for a plane shape, and resident CTAs per SM for batches.
+"""Autotuner for the staged kernel: tile width, tile order and launch form
+(one CTA per tile, k resident CTAs per SM walking tiles, or the pipelined
+ring with its staging depth and consumer groups) for a plane shape; tile
+order and resident CTAs per SM for batches.
 
 Each candidate is timed on the GPU with the plan's kernel events (device time
 of the kernel launches only); the best choice is cached in a JSON file keyed
@@ -8,6 +10,7 @@ Cache: $HS_TUNE_CACHE, else ~/.cache/paper_1805_12258_gb300/tune.json.
 """
 from __future__ import annotations
 
+import itertools
 import json
 import math
 import os
@@ -19,8 +22,11 @@ from . import hs
 
 _lock = threading.Lock()
 
-PLANE_SPACE = {"tile_bins": (64, 96, 128), "order": (1, 2), "grid_per_sm": (0, 2, 3, 4)}
-BATCH_SPACE = {"grid_per_sm": (0, 3, 6)}
+# launch forms: one CTA per tile, resident CTAs walking tiles, pipelined ring
+LAUNCH_FORMS = ({"grid_per_sm": 0}, {"grid_per_sm": 3}, {"stages": 3, "z_split": 2},
+                {"stages": 3, "z_split": 3})
+PLANE_SPACE = {"tile_bins": (64, 96, 128), "order": (1, 2), "launch": LAUNCH_FORMS}
+BATCH_SPACE = {"order": (1, 2), "grid_per_sm": (0, 3, 6)}
 
 
 def cache_path() -> str:
@@ -85,17 +91,18 @@ def tune_plane(n_templates, n_bins, H, thresholds, *, dtype="f32", fop=None, rep
             fop = fop.to(torch.bfloat16)
         elif dtype == "f16":
             fop = fop.to(torch.float16)
-    space = space or PLANE_SPACE
+    space = dict(space or PLANE_SPACE)
+    if "grid_per_sm" in space:  # older form of the space: resident CTAs only
+        space["launch"] = tuple({"grid_per_sm": g} for g in space.pop("grid_per_sm"))
     table = []
-    for tb in space["tile_bins"]:
-        for order in space["order"]:
-            for gps in space["grid_per_sm"]:
-                opts = {"tile_bins": tb, "order": order, "grid_per_sm": gps}
-                try:
-                    ms, _ = _time_plan(fop, thresholds, n_templates, n_bins, H, dtype, reps, **opts)
-                except hs.HsError:
-                    ms = math.inf
-                table.append((opts, ms))
+    for tb, order, launch in itertools.product(space["tile_bins"], space["order"],
+                                               space["launch"]):
+        opts = {"tile_bins": tb, "order": order, **launch}
+        try:  # combinations without a compiled kernel are skipped
+            ms, _ = _time_plan(fop, thresholds, n_templates, n_bins, H, dtype, reps, **opts)
+        except hs.HsError:
+            ms = math.inf
+        table.append((opts, ms))
     best = min(table, key=lambda x: x[1])[0]
     _store(key, {"best": best, "table": table})
     return best, table
@@ -111,8 +118,8 @@ def tune_batch(n_templates, H, thresholds, beams, *, dtype="f32", reps=5, use_ca
         return _load()[key]["best"], _load()[key]["table"]
     space = space or BATCH_SPACE
     table = []
-    for gps in space["grid_per_sm"]:
-        with hs.Batch(n_templates, H, thresholds, dtype=dtype, grid_per_sm=gps,
+    for order, gps in itertools.product(space.get("order", (0,)), space["grid_per_sm"]):
+        with hs.Batch(n_templates, H, thresholds, dtype=dtype, grid_per_sm=gps, order=order,
                       max_beams=len(beams)) as b:
             b.set_beams(beams)
             b.run()
@@ -123,7 +130,7 @@ def tune_batch(n_templates, H, thresholds, beams, *, dtype="f32", reps=5, use_ca
                 b.run()
             e1.record()
             torch.cuda.synchronize()
-            table.append(({"grid_per_sm": gps}, e0.elapsed_time(e1) / reps))
+            table.append(({"order": order, "grid_per_sm": gps}, e0.elapsed_time(e1) / reps))
     best = min(table, key=lambda x: x[1])[0]
     _store(key, {"best": best, "table": table})
     return best, table

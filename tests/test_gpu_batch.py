@@ -146,3 +146,7 @@ def test_autotuner_picks_a_measured_option(tmp_path, monkeypatch):
     assert min(t[1] for t in table) < float("inf")
     best2, _ = autotune.tune_plane(85, 1 << 16, 16, ta)  # cached
     assert best2 == best
+    # the default space also times the pipelined ring (staging depth, groups)
+    best3, table3 = autotune.tune_plane(85, 1 << 16, 16, ta, reps=2, use_cache=False)
+    assert any(t[0].get("stages") == 3 and t[1] < float("inf") for t in table3)
+    assert best3 in [t[0] for t in table3]
