@@ -180,10 +180,16 @@ def host_cores():
 
 
 def kernel_source_hash():
+    """Hash of the staged kernel's code (hs_staged.cu + hs_device.cuh) with
+    comments and white space removed, so comment edits keep a profile valid."""
+    import re
     h = hashlib.sha256()
     for f in ("hs_staged.cu", "hs_device.cuh"):
-        with open(os.path.join(ROOT, "paper_1805_12258_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1805_12258_gb300", "csrc", f)) as fh:
+            code = fh.read()
+        code = re.sub(r"/\*.*?\*/", "", code, flags=re.S)
+        code = re.sub(r"//[^\n]*", "", code)
+        h.update(re.sub(r"\s+", "", code).encode())
     return h.hexdigest()[:16]
 
 

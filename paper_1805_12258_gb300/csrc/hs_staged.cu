@@ -20,8 +20,10 @@
 // group bound (a few values in registers; per-row bounds would have to be
 // re-read for every row and cost more than they save).  The fast pass forms
 // HP_b only at the group ends (each group summed as a tree with packed FP32
-// adds over the pair, the bound lowered by that order's FP32 error) and marks
-// the row pairs that might hold a hit; the slow pass recomputes those rows
+// adds over the pair; each group's bound rides in the value of its first
+// level, so a group's test is the sign of the running sum, the bounds lowered
+// by the FP32 error of that order) and marks the row pairs that might hold a
+// hit; the slow pass recomputes those rows
 // level by level in ascending m (the order of Eq. 2) and appends the true
 // hits with warp ballot + prefix and one atomic per warp.  A thread that
 // loaded any value with its sign bit set (a negative input or -0) sends all
@@ -29,6 +31,11 @@
 // non-negative.  For 16-bit planes the bounds are lowered by the storage
 // error too and the slow pass re-evaluates possible hits from the FP32 copy,
 // so candidates match the FP32 path record for record.
+//
+// Kernels: staged_kernel (one plane; one CTA per tile, or resident CTAs
+// walking the tile order), pipe_kernel (one plane; a persistent CTA per SM
+// with a producer warp and a ring of stages), batched_kernel (many planes,
+// descriptors in the launch's parameter block).
 #include <algorithm>
 #include <cstring>
 
