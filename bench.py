@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--index", default="stretch", choices=["stretch", "hfrac"],
                     help="index map: the paper's stretch (Eq. 1-2) or harmonic fractions")
     ap.add_argument("--kernel", default="auto", choices=["auto", "staged", "generic"])
+    ap.add_argument("--check-signs", action="store_true",
+                    help="keep the staged kernel's per-value sign check (by default the plan "
+                         "declares the plane non-negative: the synthetic planes are powers)")
     ap.add_argument("--stages", type=int, default=0,
                     help="staged kernel: ring stages of the pipelined variant (0: one CTA per tile)")
     ap.add_argument("--z-split", type=int, default=0,
@@ -301,7 +304,7 @@ def run_ours(args):
     cands = hs.CandBuffer(1 << 20)
     plan = hs.Plan(nt, n, H, ta, dtype=args.dtype, order=args.order, tile_bins=args.tile_bins,
                    grid_per_sm=args.grid_per_sm or 0, stages=args.stages, z_split=args.z_split,
-                   index=args.index, kernel=args.kernel)
+                   index=args.index, kernel=args.kernel, assume_nonneg=not args.check_signs)
     stream = torch.cuda.current_stream()
 
     f_lo, f_hi = shard.band_bounds(n, ws, plan.tile_bins)[rank] if band else (0, n)
@@ -442,6 +445,8 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": wl.name, "n_templates": nt, "n_bins": n, "H": H,
                        "p_fa": wl.p_fa, "kernel": plan.kernel, "index": args.index,
+                       "inputs": ("checked for negative values" if args.check_signs else
+                                  "declared non-negative (powers; plan option assume_nonneg)"),
                        "tile_bins": plan.tile_bins,
                        "order": args.order, "grid_per_sm": args.grid_per_sm or 0,
                        "candidates": n_cand,

@@ -82,6 +82,11 @@ typedef struct {
                        persistent CTA per SM with an s-stage ring of tiles, filled by a
                        producer warp while consumer groups sum */
     int z_split;    /* with stages > 0: consumer groups of tile_bins threads (0 = 2) */
+    int assume_nonneg; /* 1: the caller declares every plane value non-negative and not
+                       NaN (detected power is); the staged kernel then skips its per-value
+                       sign check (about 4 % faster; compiled for 85 x 16 and 21 x 8 at
+                       128 bins).  A plane that breaks the promise may lose candidates.
+                       0 (default): signed inputs are handled exactly. */
 } hs_options;
 
 /* Candidate record flags */

@@ -240,6 +240,7 @@ hs_status launch_range(hs_plan *p, const void *fop, const float *fop32, cudaStre
         L.tile_hi = (int)((f_hi + p->tb - 1) / p->tb);
         L.grid_per_sm = p->opt.grid_per_sm;
         L.ring_zs = p->ring_zs;
+        L.assume_nonneg = p->opt.assume_nonneg != 0;
         L.ring_stages = p->ring_stages;
         e = launch_staged(L, s);
         if (e != cudaSuccess)
@@ -319,7 +320,8 @@ hs_status hs_plan_create(hs_plan **out, int n_templates, int64_t n_bins, int H,
     if (o.dtype < HS_F32 || o.dtype > HS_F16 || o.index < 0 || o.index > 1 || o.zround < 0 ||
         o.zround > 1 || o.kernel < 0 || o.kernel > 2 || o.order < 0 || o.order > 2 ||
         o.tile_bins < 0 || o.grid_per_sm < 0 || o.grid_per_sm > 64 || o.stages < 0 ||
-        o.stages > 8 || o.z_split < 0 || o.z_split > 8)
+        o.stages > 8 || o.z_split < 0 || o.z_split > 8 || o.assume_nonneg < 0 ||
+        o.assume_nonneg > 1)
         return fail(HS_ERR_INVALID, "unknown option value");
     if (o.row_pitch != 0 && o.row_pitch < n_bins)
         return fail(HS_ERR_INVALID, "row_pitch must be 0 or at least n_bins");

@@ -69,6 +69,7 @@ struct StagedLaunch {
     int tile_lo, tile_hi;     // tiles [tile_lo, tile_hi) of the order
     int grid_per_sm;          // 0: one CTA per tile; k > 0: k resident CTAs per SM
     int ring_zs, ring_stages; // > 0: the pipelined kernel, consumer groups and stages
+    bool assume_nonneg;       // the caller declares the plane non-negative
 };
 
 // True when the pipelined kernel is compiled for this shape, groups and stages.

@@ -190,7 +190,11 @@ struct CtaOr {
     __device__ __forceinline__ bool operator()(bool v) const { return __syncthreads_or(v) != 0; }
 };
 
-template <int NT, int H, int TB, typename T, typename P, typename AnyOf = CtaOr>
+// SIGNCHK: watch every loaded value's sign bit and send a thread that saw one
+// set to the exact pass (off only when the caller declares the plane
+// non-negative).
+template <int NT, int H, int TB, typename T, typename P, typename AnyOf = CtaOr,
+          bool SIGNCHK = true>
 __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
                                          int f0, const unsigned char *smem, uint32_t bar,
                                          uint32_t parity, AnyOf any_of = AnyOf{})
@@ -281,7 +285,8 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
         static_for<0, H>([&](auto M) {
             const float v = to_f32(sm[bidx[M]]);
             put(M, v, v);
-            negbits |= __float_as_uint(v);
+            if constexpr (SIGNCHK)
+                negbits |= __float_as_uint(v);
         });
         record(std::integral_constant<int, 0>{}, pair_test());
         // pairs (+zz, -zz): reload the value of m only when m divides zz
@@ -294,7 +299,8 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
                     const float tv = to_f32(sm[bidx[M] + off]);
                     const float bv = to_f32(sm[bidx[M] - off]);
                     put(M, tv, bv);
-                    negbits |= __float_as_uint(tv) | __float_as_uint(bv);
+                    if constexpr (SIGNCHK)
+                        negbits |= __float_as_uint(tv) | __float_as_uint(bv);
                 }
             });
             record(ZZ, pair_test());
@@ -394,7 +400,7 @@ constexpr int resident_ctas()
 // One plane.  Grid-stride over the tile order: with one CTA per tile each CTA
 // sums one tile; with a smaller grid the CTAs stay resident and walk several
 // tiles, saving the launch and teardown of a CTA per tile.
-template <int NT, int H, int TB, typename T>
+template <int NT, int H, int TB, typename T, bool SIGNCHK = true>
 __global__ void __launch_bounds__(TB, (resident_ctas<NT, H, TB, T>()))
     staged_kernel(const __grid_constant__ Params<NT, H, T> p)
 {
@@ -414,7 +420,8 @@ __global__ void __launch_bounds__(TB, (resident_ctas<NT, H, TB, T>()))
         const int f0 = (p.order ? (int)__ldg(p.order + slot) : slot) * TB;
         if (threadIdx.x == 0)
             issue_tile<NT, H, TB, T>(tt, f0, sbase, bar);
-        if (!sum_tile<NT, H, TB, T>(p, tt, f0, smem, bar, parity))
+        if (!sum_tile<NT, H, TB, T, Params<NT, H, T>, CtaOr, SIGNCHK>(p, tt, f0, smem, bar,
+                                                                      parity))
             break;
         __syncthreads(); // the stage is free before the next tile's boxes land
     }
@@ -595,7 +602,7 @@ __global__ void reset_counter_list(const __grid_constant__ CounterList l)
     }
 }
 
-template <int NT, int H, int TB, typename T>
+template <int NT, int H, int TB, typename T, bool SIGNCHK = true>
 cudaError_t launch_one(const StagedLaunch &a, cudaStream_t s)
 {
     using C = Cfg<NT, H, TB, T>;
@@ -618,7 +625,7 @@ cudaError_t launch_one(const StagedLaunch &a, cudaStream_t s)
     p.n_slots = a.tile_hi - a.tile_lo;
     if (p.n_slots <= 0)
         return cudaSuccess;
-    auto kern = staged_kernel<NT, H, TB, T>;
+    auto kern = staged_kernel<NT, H, TB, T, SIGNCHK>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e == cudaSuccess) // all of the unified L1/shared storage as shared memory
         e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -762,6 +769,13 @@ void box_of(int m, int *w, int *rows)
     X(21, 8, 128, __nv_bfloat16, HS_BF16)                                                     \
     X(21, 8, 128, __half, HS_F16)
 
+// Shapes with a variant for planes declared non-negative (no sign check).
+#define HS_NONNEG_SHAPES(X)                                                                   \
+    X(85, 16, 128, float, HS_F32)                                                             \
+    X(85, 16, 128, __nv_bfloat16, HS_BF16)                                                    \
+    X(85, 16, 128, __half, HS_F16)                                                            \
+    X(21, 8, 128, float, HS_F32)
+
 // Pipelined variants: (templates, levels, tile bins, consumer groups,
 // stages, type).
 #define HS_PIPE_SHAPES(X)                                                                     \
@@ -874,6 +888,13 @@ cudaError_t launch_staged(const StagedLaunch &a, cudaStream_t s)
         return cudaErrorInvalidValue;
     }
     const StagedShape &sh = a.sh;
+    if (a.assume_nonneg && a.grid_per_sm == 0) {
+#define X(NT_, H_, TB_, T_, DT_)                                                              \
+        if (sh.nt == NT_ && sh.H == H_ && sh.tb == TB_ && sh.dtype == DT_)                   \
+            return launch_one<NT_, H_, TB_, T_, false>(a, s);
+        HS_NONNEG_SHAPES(X)
+#undef X
+    }
 #define X(NT_, H_, TB_, T_, DT_)                                                              \
     if (sh.nt == NT_ && sh.H == H_ && sh.tb == TB_ && sh.dtype == DT_)                       \
         return launch_one<NT_, H_, TB_, T_>(a, s);

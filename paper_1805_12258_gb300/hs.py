@@ -50,7 +50,8 @@ class hs_options(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int), ("index", ctypes.c_int), ("zround", ctypes.c_int),
                 ("kernel", ctypes.c_int), ("tile_bins", ctypes.c_int), ("order", ctypes.c_int),
                 ("grid_per_sm", ctypes.c_int), ("row_pitch", ctypes.c_int),
-                ("stages", ctypes.c_int), ("z_split", ctypes.c_int)]
+                ("stages", ctypes.c_int), ("z_split", ctypes.c_int),
+                ("assume_nonneg", ctypes.c_int)]
 
 
 class hs_cand(ctypes.Structure):
@@ -342,10 +343,10 @@ class Plan:
 
     def __init__(self, n_templates, n_bins, H, thresholds, *, dtype="f32", index="stretch",
                  zround="symmetric", kernel="auto", tile_bins=0, order=0, grid_per_sm=0,
-                 row_pitch=0, stages=0, z_split=0):
+                 row_pitch=0, stages=0, z_split=0, assume_nonneg=False):
         opt = hs_options(DTYPES[dtype], INDEX[index], ZROUND[zround], KERNELS[kernel],
                          int(tile_bins), int(order), int(grid_per_sm), int(row_pitch),
-                         int(stages), int(z_split))
+                         int(stages), int(z_split), int(bool(assume_nonneg)))
         self.n_templates, self.n_bins, self.H = n_templates, n_bins, H
         self.dtype = dtype
         self.handle = hs_plan_create(n_templates, n_bins, H, thresholds, opt)
@@ -419,7 +420,7 @@ class Batch:
         ta = np.ascontiguousarray(thresholds, dtype=np.float32)
         if ta.shape != (H, n_templates):
             raise ValueError(f"thresholds must have shape {(H, n_templates)}, got {ta.shape}")
-        opt = hs_options(DTYPES[dtype], 0, 0, 0, 0, int(order), int(grid_per_sm), 0, 0, 0)
+        opt = hs_options(DTYPES[dtype], 0, 0, 0, 0, int(order), int(grid_per_sm), 0, 0, 0, 0)
         out = ctypes.c_void_p()
         _batch_check(lib().hs_batch_create(ctypes.byref(out), n_templates, H, ta.ctypes.data,
                                            ctypes.byref(opt), int(max_beams)), "hs_batch_create")

@@ -32,7 +32,7 @@ def test_library_exports_every_declared_symbol(L):
 def test_record_layout():
     assert ctypes.sizeof(hs.hs_cand) == 16
     assert hs.CAND_DTYPE.itemsize == 16
-    assert ctypes.sizeof(hs.hs_options) == 40
+    assert ctypes.sizeof(hs.hs_options) == 44
 
 
 def test_status_strings(L):

@@ -116,6 +116,24 @@ def test_other_index_maps(index, zround, nt, n, H):
     np.testing.assert_allclose(got, ref, rtol=RTOL, atol=0)
 
 
+@pytest.mark.parametrize("nt,n,H,dtype", [(85, 20000, 16, "f32"), (21, 50000, 8, "f32"),
+                                          (85, 8192, 16, "bf16")])
+def test_declared_nonnegative_planes_same_records(nt, n, H, dtype):
+    # assume_nonneg skips the per-value sign check: on a non-negative plane
+    # the records are those of the checked kernel (and the oracle's)
+    plane = synth.noise(nt, n, seed=53)
+    ta = synth.thresholds(1e-4, H, nt)
+    fop = plane if dtype == "f32" else _bf16_bits(plane)
+    fop32 = None if dtype == "f32" else plane
+    a, na, _, _ = run_gpu(fop, H, ta, dtype=dtype, fop32=fop32)
+    b, nb, st, used = run_gpu(fop, H, ta, dtype=dtype, fop32=fop32, assume_nonneg=True)
+    assert used == "staged" and st == hs.HS_OK and na == nb > 0
+    assert np.array_equal(a, b)
+    if dtype == "f32":
+        ref, near = oracle.detect(plane, H, ta, threads=8)
+        assert_matches_oracle(b, ref, near)
+
+
 def test_signed_inputs_take_the_exact_path():
     # Negative inputs void the monotone-sum prefilter; the staged kernel must
     # notice and test every level exactly.
