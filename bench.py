@@ -507,11 +507,12 @@ def run_batch(args):
     gps, order = args.grid_per_sm, args.order
     tuned = None
     if gps is None or gps < 0:  # the autotuner chooses tile order and grid
-        best, table = autotune.tune_batch(nt, H, ta, beams)
+        best, table = autotune.tune_batch(nt, H, ta, beams, assume_nonneg=not args.check_signs)
         gps, order = best["grid_per_sm"], best.get("order", args.order)
         tuned = table
     stream = torch.cuda.current_stream()
-    with hs.Batch(nt, H, ta, grid_per_sm=gps, max_beams=len(beams), order=order) as batch:
+    with hs.Batch(nt, H, ta, grid_per_sm=gps, max_beams=len(beams), order=order,
+                  assume_nonneg=not args.check_signs) as batch:
         batch.set_beams(beams)
         for _ in range(max(3, args.warmup)):
             batch.graph_run(stream)
@@ -532,7 +533,8 @@ def run_batch(args):
         tiles = batch.tiles
         launches = batch.launches
     # the same beams one hs_run each, back to back on the stream
-    plans = [hs.Plan(nt, n, H, ta, row_pitch=dev.shape[1]) for dev, n, _ in beams]
+    plans = [hs.Plan(nt, n, H, ta, row_pitch=dev.shape[1], assume_nonneg=not args.check_signs)
+             for dev, n, _ in beams]
     try:
         def sequential():
             for plan, (dev, n, cb) in zip(plans, beams):
@@ -561,6 +563,8 @@ def run_batch(args):
                                f"log-uniform in [2^{lo:g}, 2^{hi:g}], H=16 fp32",
                    "beams": len(beams), "bins_total": sum(sizes), "tiles": tiles,
                    "launches_per_step": 1 + launches,
+                   "inputs": "checked for negative values" if args.check_signs else
+                             "declared non-negative (powers)",
                    "tile_order": "linear" if order == 1 else "octave-interleaved",
                    "grid_per_sm": gps, "graph": True, "candidates": n_cand,
                    "l2": "inputs larger than L2, no flush"},
@@ -606,7 +610,7 @@ def run_serve(args):
 
     n_max = int(round(2.0 ** hi))
     with hs.Server(nt, H, ta, n_slots=args.slots, slot_bins=n_max, cand_capacity=4096,
-                   queue_limit=1 << 16) as srv:
+                   queue_limit=1 << 16, assume_nonneg=not args.check_signs) as srv:
         # warm-up: every path once (allocations, first launches)
         wn, wd, ws = draw(2 * args.slots)
         warm = [srv.submit(10**6 + i, int(wn[i]), str(wd[i]), int(ws[i])) for i in range(len(wn))]
@@ -754,7 +758,9 @@ def run_serve(args):
         "config": {"workload": f"serving: Poisson {args.serve_rate:g} beams/s for "
                                f"{args.serve_seconds:g} s, 85 templates x n_bins log-uniform in "
                                f"[2^{lo:g}, 2^{hi:g}], H=16, FP32/BF16 50/50, 0-10 signals",
-                   "slots": args.slots, "l2": "inputs larger than L2"},
+                   "slots": args.slots, "l2": "inputs larger than L2",
+                   "inputs": "checked for negative values" if args.check_signs else
+                             "declared non-negative (powers)"},
         "open_loop": dict(so, rejected=rej, offered_per_s=args.serve_rate),
         "closed_loop": sc,
         "closed_loop_resident_planes": dict(sr, note="planes made beforehand and kept "

@@ -201,8 +201,9 @@ typedef struct hs_batch hs_batch;
 
 /* Create a batch for up to max_beams beams (1..65536) of n_templates rows and
  * H levels with thresholds TA[H][n_templates] (copied).  opt: dtype, order
- * (tile order inside each beam, as for a plan) and grid_per_sm (0 = one CTA
- * per tile; k > 0 = k resident CTAs per SM).  Compiled shapes: 85 x 16 (FP32,
+ * (tile order inside each beam, as for a plan), grid_per_sm (0 = one CTA
+ * per tile; k > 0 = k resident CTAs per SM) and assume_nonneg (as for a
+ * plan).  Compiled shapes: 85 x 16 (FP32,
  * BF16) and 21 x 8 (FP32), stretch index map, symmetric rounding.
  * Errors: HS_ERR_INVALID, HS_ERR_UNSUPPORTED, HS_ERR_OOM, HS_ERR_CUDA. */
 HS_API hs_status hs_batch_create(hs_batch **out, int n_templates, int H, const float *thresholds,
@@ -259,6 +260,9 @@ typedef struct {
     uint32_t cand_capacity;   /* records kept per request (1..2^20) */
     int queue_limit;          /* requests waiting for a slot (>= 0) */
     int max_group;            /* requests admitted into one group (0 = n_slots) */
+    int assume_nonneg;        /* 1: resident planes brought by requests are non-negative
+                                 (generated planes are); the kernels skip their per-value
+                                 sign check, as hs_options.assume_nonneg */
 } hs_server_config;
 
 typedef struct {

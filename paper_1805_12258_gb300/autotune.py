@@ -109,18 +109,19 @@ def tune_plane(n_templates, n_bins, H, thresholds, *, dtype="f32", fop=None, rep
 
 
 def tune_batch(n_templates, H, thresholds, beams, *, dtype="f32", reps=5, use_cache=True,
-               space=None):
+               space=None, assume_nonneg=False):
     """Best resident CTAs per SM for a batch of beams [(fop, n_bins, CandBuffer), ...]."""
     import torch
     n_rep = int(np.median([b[1] for b in beams]))
-    key = key_of(f"batch{len(beams)}", n_templates, H, dtype, n_rep)
+    key = key_of(f"batch{len(beams)}{'+' if assume_nonneg else ''}", n_templates, H, dtype,
+                 n_rep)
     if use_cache and key in _load():
         return _load()[key]["best"], _load()[key]["table"]
     space = space or BATCH_SPACE
     table = []
     for order, gps in itertools.product(space.get("order", (0,)), space["grid_per_sm"]):
         with hs.Batch(n_templates, H, thresholds, dtype=dtype, grid_per_sm=gps, order=order,
-                      max_beams=len(beams)) as b:
+                      max_beams=len(beams), assume_nonneg=assume_nonneg) as b:
             b.set_beams(beams)
             b.run()
             torch.cuda.synchronize()

@@ -30,6 +30,7 @@ struct hs_batch {
     std::vector<uint32_t> h_order;
     std::vector<uint32_t> order_full; // order of the largest beam seen (a filter gives smaller ones)
     int grid_per_sm = 0;         // 0: one CTA per tile
+    bool assume_nonneg = false;  // planes declared non-negative: no sign check
     int sms = 0;
     std::mutex mu;
     cudaStream_t cap_stream = nullptr;
@@ -68,6 +69,7 @@ StagedBatch launch_args(const hs_batch *b)
     a.order = b->order == 1 ? nullptr : b->d_order;
     a.grid_per_sm = b->grid_per_sm;
     a.sms = b->sms;
+    a.assume_nonneg = b->assume_nonneg;
     return a;
 }
 
@@ -96,7 +98,7 @@ hs_status hs_batch_create(hs_batch **out, int n_templates, int H, const float *t
         if (!std::isfinite(thresholds[i]))
             return fail(HS_ERR_INVALID, "thresholds must be finite");
     if (o.dtype < HS_F32 || o.dtype > HS_F16 || o.grid_per_sm < 0 || o.grid_per_sm > 64 ||
-        o.order < 0 || o.order > 2)
+        o.order < 0 || o.order > 2 || o.assume_nonneg < 0 || o.assume_nonneg > 1)
         return fail(HS_ERR_INVALID, "unknown option value");
     const StagedShape sh{n_templates, H, 128, o.dtype};
     if (!staged_batch_available(sh) || o.index != HS_INDEX_STRETCH ||
@@ -110,6 +112,7 @@ hs_status hs_batch_create(hs_batch **out, int n_templates, int H, const float *t
     b->H = H;
     b->dtype = o.dtype;
     b->order = o.order == 0 ? 2 : o.order;
+    b->assume_nonneg = o.assume_nonneg != 0;
     b->max_beams = max_beams;
     b->ta.assign(thresholds, thresholds + (size_t)H * n_templates);
     if (o.dtype == HS_BF16)

@@ -101,6 +101,7 @@ struct StagedBatch {
     const uint32_t *order;        // device: tile order of each beam, concatenated (or null)
     int grid_per_sm;              // 0: one CTA per tile; k > 0: k resident CTAs per SM
     int sms;
+    bool assume_nonneg;           // the caller declares every plane non-negative
 };
 
 bool staged_batch_available(const StagedShape &sh);

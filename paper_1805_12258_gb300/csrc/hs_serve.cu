@@ -509,6 +509,7 @@ hs_status hs_server_create(hs_server **out, const hs_server_config *cfg)
             hs_options o{};
             o.dtype = d == 0 ? HS_F32 : HS_BF16;
             o.order = s->tile_order;
+            o.assume_nonneg = c.assume_nonneg ? 1 : 0;
             const hs_status st = hs_batch_create(&s->batch[l][d], c.n_templates, c.H,
                                                  s->ta.data(), &o, group);
             if (st != HS_OK) {

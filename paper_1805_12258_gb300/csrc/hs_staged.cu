@@ -553,7 +553,7 @@ struct BatchParams {
 // walk the concatenated tiles of the launch's beams grid-stride (one tile per
 // CTA when the grid covers them) and find each tile's beam by a CTA-uniform
 // scan of the cumulative tile ends.
-template <int NT, int H, int TB, typename T>
+template <int NT, int H, int TB, typename T, bool SIGNCHK = true>
 __global__ void __launch_bounds__(TB, (resident_ctas<NT, H, TB, T>()))
     batched_kernel(const __grid_constant__ BatchParams<NT, H, T> p)
 {
@@ -580,7 +580,8 @@ __global__ void __launch_bounds__(TB, (resident_ctas<NT, H, TB, T>()))
             issue_tile<NT, H, TB, T>(tt, tile * TB, sbase, bar);
         }
         cur = b;
-        if (!sum_tile<NT, H, TB, T>(p, tt, tile * TB, smem, bar, parity))
+        if (!sum_tile<NT, H, TB, T, BatchParams<NT, H, T>, CtaOr, SIGNCHK>(p, tt, tile * TB,
+                                                                           smem, bar, parity))
             break;
         __syncthreads();
     }
@@ -685,7 +686,7 @@ cudaError_t launch_pipe(const StagedLaunch &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <int NT, int H, int TB, typename T>
+template <int NT, int H, int TB, typename T, bool SIGNCHK = true>
 cudaError_t launch_batch_one(const StagedBatch &a, cudaStream_t s)
 {
     using C = Cfg<NT, H, TB, T>;
@@ -702,7 +703,7 @@ cudaError_t launch_batch_one(const StagedBatch &a, cudaStream_t s)
     }
     if (e != cudaSuccess)
         return e;
-    auto kern = batched_kernel<NT, H, TB, T>;
+    auto kern = batched_kernel<NT, H, TB, T, SIGNCHK>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -847,6 +848,13 @@ bool staged_batch_available(const StagedShape &sh)
 cudaError_t launch_staged_batch(const StagedBatch &a, cudaStream_t s)
 {
     const StagedShape &sh = a.sh;
+    if (a.assume_nonneg) {
+#define X(NT_, H_, TB_, T_, DT_)                                                              \
+        if (sh.nt == NT_ && sh.H == H_ && sh.tb == TB_ && sh.dtype == DT_)                   \
+            return launch_batch_one<NT_, H_, TB_, T_, false>(a, s);
+        HS_BATCH_SHAPES(X)
+#undef X
+    }
 #define X(NT_, H_, TB_, T_, DT_)                                                              \
     if (sh.nt == NT_ && sh.H == H_ && sh.tb == TB_ && sh.dtype == DT_)                       \
         return launch_batch_one<NT_, H_, TB_, T_>(a, s);

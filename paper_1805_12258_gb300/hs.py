@@ -74,7 +74,8 @@ class hs_server_config(ctypes.Structure):
     _fields_ = [("n_templates", ctypes.c_int), ("H", ctypes.c_int),
                 ("thresholds", ctypes.c_void_p), ("n_slots", ctypes.c_int),
                 ("slot_bins", ctypes.c_int64), ("cand_capacity", ctypes.c_uint32),
-                ("queue_limit", ctypes.c_int), ("max_group", ctypes.c_int)]
+                ("queue_limit", ctypes.c_int), ("max_group", ctypes.c_int),
+                ("assume_nonneg", ctypes.c_int)]
 
 
 class hs_request(ctypes.Structure):
@@ -416,11 +417,12 @@ class Batch:
     descriptors; graph_run replays a captured CUDA graph of those launches."""
 
     def __init__(self, n_templates, H, thresholds, *, dtype="f32", grid_per_sm=0,
-                 max_beams=64, order=0):
+                 max_beams=64, order=0, assume_nonneg=False):
         ta = np.ascontiguousarray(thresholds, dtype=np.float32)
         if ta.shape != (H, n_templates):
             raise ValueError(f"thresholds must have shape {(H, n_templates)}, got {ta.shape}")
-        opt = hs_options(DTYPES[dtype], 0, 0, 0, 0, int(order), int(grid_per_sm), 0, 0, 0, 0)
+        opt = hs_options(DTYPES[dtype], 0, 0, 0, 0, int(order), int(grid_per_sm), 0, 0, 0,
+                         int(bool(assume_nonneg)))
         out = ctypes.c_void_p()
         _batch_check(lib().hs_batch_create(ctypes.byref(out), n_templates, H, ta.ctypes.data,
                                            ctypes.byref(opt), int(max_beams)), "hs_batch_create")
@@ -493,12 +495,13 @@ class Server:
     kernels, and a completion thread that returns candidates to the host."""
 
     def __init__(self, n_templates, H, thresholds, *, n_slots=16, slot_bins=1 << 22,
-                 cand_capacity=4096, queue_limit=1024, max_group=0):
+                 cand_capacity=4096, queue_limit=1024, max_group=0, assume_nonneg=False):
         ta = np.ascontiguousarray(thresholds, dtype=np.float32)
         if ta.shape != (H, n_templates):
             raise ValueError(f"thresholds must have shape {(H, n_templates)}, got {ta.shape}")
         cfg = hs_server_config(n_templates, H, ta.ctypes.data, int(n_slots), int(slot_bins),
-                               int(cand_capacity), int(queue_limit), int(max_group))
+                               int(cand_capacity), int(queue_limit), int(max_group),
+                               int(bool(assume_nonneg)))
         out = ctypes.c_void_p()
         st = lib().hs_server_create(ctypes.byref(out), ctypes.byref(cfg))
         if st != HS_OK:

@@ -40,13 +40,15 @@ def _plan_records(plane, H, ta):
     return recs
 
 
-@pytest.mark.parametrize("nt,H,gps", [(85, 16, 0), (85, 16, 3), (21, 8, 0)])
-def test_batch_matches_per_plane_runs_and_graph_replay(nt, H, gps):
+@pytest.mark.parametrize("nt,H,gps,nonneg", [(85, 16, 0, False), (85, 16, 3, False),
+                                             (21, 8, 0, False), (85, 16, 0, True),
+                                             (21, 8, 0, True)])
+def test_batch_matches_per_plane_runs_and_graph_replay(nt, H, gps, nonneg):
     rng = np.random.default_rng(nt)
     ta = synth.thresholds(1e-4, H, nt)
     sizes_a = [int(x) for x in rng.integers(1000, 40000, size=5)] + [129, 7]
     sizes_b = [int(x) for x in rng.integers(500, 60000, size=3)]
-    with hs.Batch(nt, H, ta, max_beams=16, grid_per_sm=gps) as batch:
+    with hs.Batch(nt, H, ta, max_beams=16, grid_per_sm=gps, assume_nonneg=nonneg) as batch:
         for rnd, sizes in enumerate((sizes_a, sizes_b, sizes_a)):
             beams, planes, bufs = [], [], []
             for i, n in enumerate(sizes):

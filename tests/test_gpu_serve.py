@@ -149,7 +149,8 @@ def test_alone_equals_in_mix():
     assert max(r[0]["group_size"] for r in results.values()) > 1  # groups did form
 
 
-def test_resident_planes_are_summed_in_place():
+@pytest.mark.parametrize("nonneg", [False, True])
+def test_resident_planes_are_summed_in_place(nonneg):
     # requests that bring a plane already in device memory (made upstream),
     # FP32 and BF16 with its FP32 copy, mixed with generated ones: each gives
     # the records of an hs_run of its plane
@@ -158,7 +159,8 @@ def test_resident_planes_are_summed_in_place():
     for i, (n, dt) in enumerate([(70001, "f32"), (50000, "bf16"), (123457, "f32")]):
         f32, bf = _plane(300 + i, n, dt, n_signals=4)
         planes.append((n, dt, f32, bf))
-    with hs.Server(NT, H, ta, n_slots=4, slot_bins=1 << 17, cand_capacity=1 << 14) as srv:
+    with hs.Server(NT, H, ta, n_slots=4, slot_bins=1 << 17, cand_capacity=1 << 14,
+                   assume_nonneg=nonneg) as srv:
         tickets = []
         for i, (n, dt, f32, bf) in enumerate(planes):
             tickets.append(srv.submit(0, n, dt, 0, fop=f32 if dt == "f32" else bf,
