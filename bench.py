@@ -38,6 +38,7 @@ sys.path.insert(0, ROOT)
 METRIC = "FOP points harmonic-summed/s (H=16) and effective HBM GB/s vs 8 TB/s"
 UNIT = "points/s"
 L2_BYTES = 129 * 2**20
+ORDER_NAMES = {0: "semitone", 1: "linear", 2: "octave", 3: "semitone"}
 
 
 def parse():
@@ -565,7 +566,7 @@ def run_batch(args):
                    "launches_per_step": 1 + launches,
                    "inputs": "checked for negative values" if args.check_signs else
                              "declared non-negative (powers)",
-                   "tile_order": "linear" if order == 1 else "octave-interleaved",
+                   "tile_order": ORDER_NAMES.get(order, str(order)),
                    "grid_per_sm": gps, "graph": True, "candidates": n_cand,
                    "l2": "inputs larger than L2, no flush"},
         "sequential_hs_run_ms": t_seq, "batch_speedup_vs_sequential": t_seq / ms,

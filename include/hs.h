@@ -73,7 +73,9 @@ typedef struct {
     int zround;     /* hs_zround (default HS_ZROUND_SYMMETRIC) */
     int kernel;     /* hs_kernel: AUTO picks the staged kernel when it applies */
     int tile_bins;  /* bins per CTA of the staged kernel: 0 = default */
-    int order;      /* tile order: 0 = default (octave), 1 = linear, 2 = octave-interleaved */
+    int order;      /* tile order: 0 = default (semitone), 1 = linear, 2 = octave (mantissa of
+                       the tile index), 3 = semitone (fractional part of 12 log2 of the
+                       tile index) */
     int grid_per_sm;/* staged kernel: 0 = one CTA per tile; k > 0 = k resident CTAs per SM
                        that walk the tiles */
     int row_pitch;  /* elements between plane rows (0 = n_bins); >= n_bins.  The staged

@@ -139,6 +139,13 @@ int hs::group_bounds(const float *ta, int n_templates, int H, float delta, float
 }
 
 namespace hs {
+// Tile order (kind 1 linear).  A tile at bin f reads the span at f/m for
+// every m, which an earlier tile read in full; the orders put those tiles
+// close in time so the span is still in L2.  Kind 2 (octave) sorts by the
+// mantissa of the tile index, which serves m = 2, 4, 8, 16 exactly; kind 3
+// (semitone) sorts by the fractional part of 12 log2(t), which also serves
+// m = 3, 6, 9, 12 to within 0.02 of the period and m = 5, 10, 15 to within
+// 0.14.
 std::vector<uint32_t> tile_order(int n_tiles, int kind)
 {
     std::vector<uint32_t> o(n_tiles);
@@ -153,6 +160,20 @@ std::vector<uint32_t> tile_order(int n_tiles, int kind)
         };
         std::stable_sort(o.begin(), o.end(),
                          [&](uint32_t a, uint32_t b) { return key(a) < key(b); });
+    } else if (kind == 3) {
+        // position of t within a twelfth of an octave: t, 2t, 4t, ... share
+        // it exactly and 3t, 6t, 9t, 12t nearly (2^(19/12) = 2.9966)
+        auto key = [](uint32_t t) {
+            if (t == 0)
+                return -1.0;
+            const double l = 12.0 * std::log2((double)t);
+            return l - std::floor(l);
+        };
+        std::vector<double> k(n_tiles);
+        for (int t = 0; t < n_tiles; ++t)
+            k[t] = key((uint32_t)t);
+        std::stable_sort(o.begin(), o.end(),
+                         [&](uint32_t a, uint32_t b) { return k[a] < k[b]; });
     }
     return o;
 }
@@ -182,9 +203,6 @@ hs_status encode_maps(hs_plan *p, const void *fop)
     return HS_OK;
 }
 
-// Tile order: linear, or octave-interleaved (tiles sorted by the mantissa of
-// their index, then by octave) so that the tiles reading a span at f/2, f/4,
-// ... run close in time to the tile that reads it at f.
 hs_status check_cands(const hs_cand_buf *c)
 {
     if (!c || !c->count)
@@ -318,7 +336,7 @@ hs_status hs_plan_create(hs_plan **out, int n_templates, int64_t n_bins, int H,
     if (!thresholds)
         return fail(HS_ERR_INVALID, "thresholds is null");
     if (o.dtype < HS_F32 || o.dtype > HS_F16 || o.index < 0 || o.index > 1 || o.zround < 0 ||
-        o.zround > 1 || o.kernel < 0 || o.kernel > 2 || o.order < 0 || o.order > 2 ||
+        o.zround > 1 || o.kernel < 0 || o.kernel > 2 || o.order < 0 || o.order > 3 ||
         o.tile_bins < 0 || o.grid_per_sm < 0 || o.grid_per_sm > 64 || o.stages < 0 ||
         o.stages > 8 || o.z_split < 0 || o.z_split > 8 || o.assume_nonneg < 0 ||
         o.assume_nonneg > 1)
@@ -394,7 +412,7 @@ hs_status hs_plan_create(hs_plan **out, int n_templates, int64_t n_bins, int H,
         p->groups = group_bounds(p->ta.data(), n_templates, H, p->delta, p->band_abs,
                                  p->tmin.data());
         p->n_tiles = (int)((n_bins + p->tb - 1) / p->tb);
-        const int kind = o.order == 0 ? 2 : o.order; // default: octave-interleaved
+        const int kind = o.order == 0 ? 3 : o.order; // default: semitone
         std::vector<uint32_t> ord = tile_order(p->n_tiles, kind);
         e = cudaMalloc(&p->d_order, sizeof(uint32_t) * ord.size());
         if (e == cudaSuccess)

@@ -98,7 +98,7 @@ hs_status hs_batch_create(hs_batch **out, int n_templates, int H, const float *t
         if (!std::isfinite(thresholds[i]))
             return fail(HS_ERR_INVALID, "thresholds must be finite");
     if (o.dtype < HS_F32 || o.dtype > HS_F16 || o.grid_per_sm < 0 || o.grid_per_sm > 64 ||
-        o.order < 0 || o.order > 2 || o.assume_nonneg < 0 || o.assume_nonneg > 1)
+        o.order < 0 || o.order > 3 || o.assume_nonneg < 0 || o.assume_nonneg > 1)
         return fail(HS_ERR_INVALID, "unknown option value");
     const StagedShape sh{n_templates, H, 128, o.dtype};
     if (!staged_batch_available(sh) || o.index != HS_INDEX_STRETCH ||
@@ -111,7 +111,7 @@ hs_status hs_batch_create(hs_batch **out, int n_templates, int H, const float *t
     b->nt = n_templates;
     b->H = H;
     b->dtype = o.dtype;
-    b->order = o.order == 0 ? 2 : o.order;
+    b->order = o.order == 0 ? 3 : o.order; // default: semitone
     b->assume_nonneg = o.assume_nonneg != 0;
     b->max_beams = max_beams;
     b->ta.assign(thresholds, thresholds + (size_t)H * n_templates);
@@ -157,7 +157,7 @@ hs_status hs::batch_set_prepared(hs_batch *b, const StagedBatchBeam *beams, int 
     std::lock_guard<std::mutex> lk(b->mu);
     cudaError_t e = cudaSuccess;
     if (b->order != 1) {
-        // the octave order of t < k tiles is the octave order of more tiles
+        // the order of t < k tiles is the order of more tiles
         // with the entries >= k dropped (the sort key depends on t alone)
         int most = 0;
         for (const StagedBatchBeam &d : nb)

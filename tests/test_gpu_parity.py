@@ -343,16 +343,17 @@ def test_pipelined_matches_oracle_on_the_small_ska_slice():
     assert_matches_oracle(recs, ref, near)
 
 
+@pytest.mark.parametrize("order", [2, 3])
 @pytest.mark.parametrize("n", [1 << 15, (1 << 15) + 128, 1 << 18])
-def test_tile_orders_give_the_same_records(n):
-    # the octave-interleaved order (the plan's tile table) visits every tile
+def test_tile_orders_give_the_same_records(n, order):
+    # the octave and semitone orders (the plan's tile table) visit every tile
     # exactly once: the same records as the linear order
     plane = synth.noise(85, n, seed=29)
     ta = synth.thresholds(1e-4, 16, 85)
     lin, nl, _, _ = run_gpu(plane, 16, ta, order=1)
-    oct_, no, st, used = run_gpu(plane, 16, ta, order=2)
+    other, no, st, used = run_gpu(plane, 16, ta, order=order)
     assert used == "staged" and st == hs.HS_OK and nl == no > 0
-    assert np.array_equal(lin, oct_)
+    assert np.array_equal(lin, other)
 
 
 @pytest.mark.parametrize("kernel", ["staged", "generic"])
