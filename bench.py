@@ -401,7 +401,8 @@ def run_ours(args):
         algo_bytes += 0  # rechecks read only near-threshold points of the FP32 copy
     peak, peak_kind = peaks()
     achieved_gbs = algo_bytes / mean_kernel_s / 1e9
-    kname = (f"staged {nt}x{n} H={H} {args.dtype} tb={plan.tile_bins}"
+    kname = (f"staged {nt}x{n} H={H} {args.dtype} tb={plan.tile_bins} "
+             f"order={ORDER_NAMES.get(args.order, args.order)}"
              if plan.kernel == "staged" else f"generic {nt}x{n} H={H} {args.dtype} {args.index}")
 
     # e2e through hs_run_host: pinned host plane -> device, sum, records -> host

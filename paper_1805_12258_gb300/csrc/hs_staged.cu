@@ -241,12 +241,9 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
     };
     uint32_t negbits = 0u;
     uint64_t mask = 0ull;
-    // How the pairs' outcomes are kept (measured choice per element type):
-    // 16-bit planes shift each pair's sign AND into clear[w] (one funnel
-    // shift per pair; set = no group can hit; pairs 0..31 in word 0, the rest
-    // in word 1) and convert once at the end; FP32 planes OR each outcome
-    // straight into the 64-bit mask.
-    constexpr bool kShiftIn = sizeof(T) == 2;
+    // Each pair's sign AND is shifted into clear[w] (one funnel shift per
+    // pair; set = no group can hit; pairs 0..31 in word 0, the rest in word
+    // 1) and turned into the mask once at the end.
     uint32_t clear[2] = {0u, 0u};
     float2 cur[H];
     auto pair_test = [&]() -> uint32_t {
@@ -264,13 +261,8 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
         return sgn; // bit 31 clear: the pair may hold a hit
     };
     auto record = [&](auto ZZ, uint32_t sgn) {
-        constexpr int zz = decltype(ZZ)::value;
-        if constexpr (kShiftIn) {
-            constexpr int w = zz < 32 ? 0 : 1;
-            clear[w] = __funnelshift_l(sgn, clear[w], 1); // (clear << 1) | sgn >> 31
-        } else {
-            mask |= (uint64_t)((~sgn) >> 31) << zz;
-        }
+        constexpr int w = decltype(ZZ)::value < 32 ? 0 : 1;
+        clear[w] = __funnelshift_l(sgn, clear[w], 1); // (clear << 1) | sgn >> 31
     };
     // the value of level m at the pair (tv, bv), with its group's bound share
     auto put = [&](auto M, float tv, float bv) {
@@ -309,13 +301,10 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
         // pairs 32 .. Z with pair zz at bit Z-zz; reverse the bits into the
         // mask (bit zz = the pair may hold a hit)
         static_assert(Z <= 63, "two mask words");
-        if constexpr (kShiftIn) {
-            constexpr int n0 = Z + 1 < 32 ? Z + 1 : 32;
-            mask = (uint64_t)(__brev(~clear[0]) >> (32 - n0));
-            if constexpr (Z >= 32)
-                mask |= (uint64_t)((__brev(~clear[1]) >> (63 - Z)) & ((1u << (Z - 31)) - 1u))
-                        << 32;
-        }
+        constexpr int n0 = Z + 1 < 32 ? Z + 1 : 32;
+        mask = (uint64_t)(__brev(~clear[0]) >> (32 - n0));
+        if constexpr (Z >= 32)
+            mask |= (uint64_t)((__brev(~clear[1]) >> (63 - Z)) & ((1u << (Z - 31)) - 1u)) << 32;
     }
     if (!ok) {
         if (tid == 0)
