@@ -38,6 +38,7 @@ struct hs_plan {
     std::mutex mu;                 // guards the descriptor cache and streams
     const void *map_ptr = nullptr; // plane the cached descriptors encode
     CUtensorMap maps[kMaxStagedH];
+    CUtensorMap split1[2]; // level 1 in row bands: centre rows, one outer side
     cudaStream_t copy_stream = nullptr;
     std::vector<cudaEvent_t> chunk_events;
     bool timing = false;             // bracket kernel launches with events
@@ -199,6 +200,20 @@ hs_status encode_maps(hs_plan *p, const void *fop)
             return fail(HS_ERR_CUDA, buf);
         }
     }
+    {
+        // level 1 in bands: rows [Z - Z/2, Z + Z/2] and Z - Z/2 rows per side
+        int w = 0, rows = 0;
+        staged_box(sh, 1, &w, &rows);
+        const int z = (p->nt - 1) / 2, rb = z / 2;
+        CUresult r = encode_tensor_map(&p->split1[0], p->opt.dtype, fop, p->n, p->ld, p->nt, w,
+                                       2 * rb + 1);
+        if (r == CUDA_SUCCESS)
+            r = encode_tensor_map(&p->split1[1], p->opt.dtype, fop, p->n, p->ld, p->nt, w, z - rb);
+        if (r != CUDA_SUCCESS) {
+            p->map_ptr = nullptr;
+            return fail(HS_ERR_CUDA, "cuTensorMapEncodeTiled failed for the level-1 bands");
+        }
+    }
     p->map_ptr = fop;
     return HS_OK;
 }
@@ -242,6 +257,7 @@ hs_status launch_range(hs_plan *p, const void *fop, const float *fop32, cudaStre
         StagedLaunch L{};
         L.sh = StagedShape{p->nt, p->H, p->tb, p->opt.dtype};
         L.maps = p->maps;
+        L.split1 = p->split1;
         L.tmin_host = p->tmin.data();
         L.fop = fop;
         L.ta = p->d_ta;

@@ -12,6 +12,9 @@ namespace hs {
 
 // Upper bound on a device wait before a kernel gives up (HS_ERR_TIMEOUT).
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+// Most tries of the mbarrier wait inside the staged kernel's walk (each may
+// suspend up to 1 ms; the wait also stops after kWaitLimitNs).
+constexpr uint32_t kBandWaitTries = 1u << 24;
 
 struct GenericArgs {
     const void *fop;      // plane [nt][n], dtype
@@ -54,6 +57,7 @@ int staged_groups(int H, int *ends);
 struct StagedLaunch {
     StagedShape sh;
     const CUtensorMap *maps;  // host copies, H descriptors (encoded for this plane)
+    const CUtensorMap *split1; // level 1 in row bands (centre, outer side), or null
     const float *tmin_host;   // prefilter thresholds [groups] (min over rows)
     const float *ta;          // device thresholds [H][nt]
     const void *fop;          // the plane (device)

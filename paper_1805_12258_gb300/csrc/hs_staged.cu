@@ -7,7 +7,11 @@
 // "necessary points" of the chunk (Section IV-C2), gathered with 2-D TMA
 // boxes instead of the paper's reordered plane -- so each plane point crosses
 // HBM about once per tile that needs it.  One elected thread issues one box
-// per m, all completing on a single mbarrier.
+// per m, all completing on a single mbarrier; or, on FP32 planes declared
+// non-negative, level 1 in three row bands: the centre rows [Z - Z/2, Z + Z/2]
+// complete with the spans of m >= 2 (whose rows all lie in that band) on one
+// mbarrier, the outer rows on a second that the walk waits for only when it
+// reaches pair Z/2 + 1, so summing starts before the outer rows land.
 //
 // Rows are walked outward from z = 0 as mirrored pairs (+zz, -zz).  Under the
 // symmetric rounding rho(z, m) = sign(z) floor(|z|/m) both rows of a pair
@@ -95,6 +99,14 @@ struct Cfg {
         return o;
     }
     static constexpr int SMEM = OFF(H + 1);
+    // Level 1 split in row bands: the centre rows [Z - RB, Z + RB] (every
+    // row the pairs zz <= RB read, with all spans m >= 2, whose rows lie
+    // within Z/2 of the centre) and the outer rows (OUT on each side).
+    static constexpr int RB = Z / 2;
+    static constexpr int OUT = Z - RB;
+    static constexpr int BYTES_CENTRE = (2 * RB + 1) * W(1) * ES;
+    static constexpr int BYTES_OUTER = OUT * W(1) * ES;
+    static constexpr int TX_CENTRE() { return TX() - BYTES(1) + BYTES_CENTRE; }
     // CTAs that fit on an SM by shared memory (228 KB, 1 KB reserved per
     // CTA), at most 8
     static constexpr int CTAS_SMEM = cmin(8, 233472 / (SMEM + 1024 + 64));
@@ -115,6 +127,7 @@ struct Cfg {
 template <int NT, int H, typename T>
 struct Params {
     CUtensorMap maps[H];    // one 2-D box per stretch factor m (its whole span)
+    CUtensorMap split1[2];  // level 1 in bands: centre rows, one outer side
     float tmin[n_groups(H)]; // prefilter bound per level group (min over rows)
     const float *ta;        // exact thresholds [H][NT] (device)
     const float *fop32;     // FP32 copy for rechecks, or null
@@ -159,6 +172,7 @@ __device__ float chain_f32(const float *fop32, int Z, long long n, int z, int f,
 // candidate buffer its hits go to (one plane for hs_run, a beam of a batch).
 struct TileTarget {
     const CUtensorMap *maps; // H descriptors (parameter or global space)
+    const CUtensorMap *split1; // level-1 band descriptors (centre, outer), or null
     const float *fop32;      // FP32 copy for rechecks (row pitch ld), or null
     long long n;             // bins of the plane
     long long ld;            // row pitch of the FP32 copy, in elements
@@ -181,6 +195,26 @@ __device__ __forceinline__ void issue_tile(const TileTarget &tt, int f0, uint32_
     });
 }
 
+// Issue the tile's boxes with level 1 in bands (thread 0): the centre band
+// and the spans m >= 2 complete on `bar`, the two outer bands on `bar_out`.
+template <int NT, int H, int TB, typename T>
+__device__ __forceinline__ void issue_tile_banded(const TileTarget &tt, int f0, uint32_t sbase,
+                                                  uint32_t bar, uint32_t bar_out)
+{
+    using C = Cfg<NT, H, TB, T>;
+    constexpr int ROWB = C::W(1) * C::ES; // bytes per level-1 row in shared memory
+    mbar_arrive_expect_tx(bar, (uint32_t)C::TX_CENTRE());
+    tma_load_2d(sbase + (C::Z - C::RB) * ROWB, &tt.split1[0], f0, C::Z - C::RB, bar);
+    static_for<2, H + 1>([&](auto M) {
+        constexpr int m = M;
+        const int x = (f0 / m) & ~(C::ALIGN - 1);
+        tma_load_2d(sbase + C::OFF(m), &tt.maps[m - 1], x, C::Z - C::R(m), bar);
+    });
+    mbar_arrive_expect_tx(bar_out, (uint32_t)(2 * C::BYTES_OUTER));
+    tma_load_2d(sbase, &tt.split1[1], f0, 0, bar_out);
+    tma_load_2d(sbase + (C::Z + C::RB + 1) * ROWB, &tt.split1[1], f0, C::Z + C::RB + 1, bar_out);
+}
+
 // Wait for the tile's stage (phase `parity` of `bar`), run the fast pass and
 // the slow pass, append the hits to tt's buffer.  Called by every thread of
 // the CTA; returns false (CTA-uniformly) if the stage did not arrive in time.
@@ -193,11 +227,14 @@ struct CtaOr {
 // SIGNCHK: watch every loaded value's sign bit and send a thread that saw one
 // set to the exact pass (off only when the caller declares the plane
 // non-negative).
+// BANDED: level 1's outer rows complete on bar_out, waited for only when the
+// walk reaches them (pair RB + 1).
 template <int NT, int H, int TB, typename T, typename P, typename AnyOf = CtaOr,
-          bool SIGNCHK = true>
+          bool SIGNCHK = true, bool BANDED = false>
 __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
                                          int f0, const unsigned char *smem, uint32_t bar,
-                                         uint32_t parity, AnyOf any_of = AnyOf{})
+                                         uint32_t parity, AnyOf any_of = AnyOf{},
+                                         uint32_t bar_out = 0u)
 {
     using C = Cfg<NT, H, TB, T>;
     constexpr int Z = C::Z;
@@ -272,6 +309,7 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
         else
             cur[M] = make_float2(tv, bv);
     };
+    bool out_ok = true;
     if (ok) {
         // template z = 0: every stretch reads the centre row
         static_for<0, H>([&](auto M) {
@@ -284,6 +322,21 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
         // pairs (+zz, -zz): reload the value of m only when m divides zz
         static_for<1, Z + 1>([&](auto ZZ) {
             constexpr int zz = ZZ;
+            if constexpr (BANDED && zz == C::RB + 1) {
+                // the outer rows: a wait bounded in time and in tries, inline
+                // (a call inside the unrolled walk would spill it); the asm's
+                // memory clobber keeps the loads below it
+                bool got = mbar_try_wait_hint(bar_out, parity, 1000000u);
+                if (!got) {
+                    const uint64_t t0 = globaltimer_ns();
+                    for (uint32_t it = 0; !got && it < kBandWaitTries; ++it) {
+                        got = mbar_try_wait_hint(bar_out, parity, 1000000u);
+                        if (!got && globaltimer_ns() - t0 > kWaitLimitNs)
+                            break;
+                    }
+                }
+                out_ok = got;
+            }
             static_for<0, H>([&](auto M) {
                 constexpr int m = M + 1;
                 if constexpr (zz % m == 0) {
@@ -305,11 +358,15 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
         mask = (uint64_t)(__brev(~clear[0]) >> (32 - n0));
         if constexpr (Z >= 32)
             mask |= (uint64_t)((__brev(~clear[1]) >> (63 - Z)) & ((1u << (Z - 31)) - 1u)) << 32;
+        if constexpr (BANDED)
+            out_ok = !any_of(!out_ok); // CTA-uniform, like ok
     }
-    if (!ok) {
+    if (!ok || !out_ok) {
         if (tid == 0)
             set_status(tt.counters, HS_ERR_TIMEOUT);
         mbar_wait_bounded(bar, parity, kWaitLimitNs); // let copies in flight land
+        if constexpr (BANDED)
+            mbar_wait_bounded(bar_out, parity, kWaitLimitNs);
         return false;
     }
     if (!valid)
@@ -389,28 +446,38 @@ constexpr int resident_ctas()
 // One plane.  Grid-stride over the tile order: with one CTA per tile each CTA
 // sums one tile; with a smaller grid the CTAs stay resident and walk several
 // tiles, saving the launch and teardown of a CTA per tile.
-template <int NT, int H, int TB, typename T, bool SIGNCHK = true>
+template <int NT, int H, int TB, typename T, bool SIGNCHK = true, bool BANDED = false>
 __global__ void __launch_bounds__(TB, (resident_ctas<NT, H, TB, T>()))
     staged_kernel(const __grid_constant__ Params<NT, H, T> p)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar_storage;
+    __shared__ __align__(8) uint64_t bar_storage[2];
     const uint32_t sbase = smem_addr(smem);
-    const uint32_t bar = smem_addr(&bar_storage);
+    const uint32_t bar = smem_addr(&bar_storage[0]);
+    const uint32_t bar_out = smem_addr(&bar_storage[1]);
     if (threadIdx.x == 0) {
         static_for<0, H>([&](auto M) { prefetch_tmap(&p.maps[M]); });
         mbar_init(bar, 1);
+        if constexpr (BANDED) {
+            prefetch_tmap(&p.split1[0]);
+            prefetch_tmap(&p.split1[1]);
+            mbar_init(bar_out, 1);
+        }
     }
     __syncthreads();
-    const TileTarget tt{p.maps, p.fop32, p.n, p.ld, p.rec, p.counters, p.cap};
+    const TileTarget tt{p.maps, p.split1, p.fop32, p.n, p.ld, p.rec, p.counters, p.cap};
     uint32_t parity = 0;
     for (int i = (int)blockIdx.x; i < p.n_slots; i += (int)gridDim.x, parity ^= 1u) {
         const int slot = p.tile_lo + i;
         const int f0 = (p.order ? (int)__ldg(p.order + slot) : slot) * TB;
-        if (threadIdx.x == 0)
-            issue_tile<NT, H, TB, T>(tt, f0, sbase, bar);
-        if (!sum_tile<NT, H, TB, T, Params<NT, H, T>, CtaOr, SIGNCHK>(p, tt, f0, smem, bar,
-                                                                      parity))
+        if (threadIdx.x == 0) {
+            if constexpr (BANDED)
+                issue_tile_banded<NT, H, TB, T>(tt, f0, sbase, bar, bar_out);
+            else
+                issue_tile<NT, H, TB, T>(tt, f0, sbase, bar);
+        }
+        if (!sum_tile<NT, H, TB, T, Params<NT, H, T>, CtaOr, SIGNCHK, BANDED>(
+                p, tt, f0, smem, bar, parity, CtaOr{}, bar_out))
             break;
         __syncthreads(); // the stage is free before the next tile's boxes land
     }
@@ -437,7 +504,7 @@ __global__ void __launch_bounds__(NC *TB + 32, 1)
     __shared__ __align__(8) uint64_t full_bar[S], empty_bar[S];
     __shared__ int issued; // iterations the producer issued
     const uint32_t sbase = smem_addr(smem);
-    const TileTarget tt{p.maps, p.fop32, p.n, p.ld, p.rec, p.counters, p.cap};
+    const TileTarget tt{p.maps, nullptr, p.fop32, p.n, p.ld, p.rec, p.counters, p.cap};
     const int G = (int)gridDim.x;
     const int n_it = (int)blockIdx.x < p.n_slots ? (p.n_slots - 1 - (int)blockIdx.x) / G + 1 : 0;
     auto tile_f0 = [&](int j) {
@@ -562,7 +629,7 @@ __global__ void __launch_bounds__(TB, (resident_ctas<NT, H, TB, T>()))
         const BeamParam<H> &bp = p.beam[b];
         const int local = i - (b ? p.beam[b - 1].tile_end : 0);
         const int tile = p.order ? (int)__ldg(p.order + p.slot_base + i) : local;
-        const TileTarget tt{bp.maps, bp.fop32, bp.n, bp.ld, bp.rec, bp.counters, bp.cap};
+        const TileTarget tt{bp.maps, nullptr, bp.fop32, bp.n, bp.ld, bp.rec, bp.counters, bp.cap};
         if (threadIdx.x == 0) {
             if (b != cur)
                 static_for<0, H>([&](auto M) { prefetch_tmap(&bp.maps[M]); });
@@ -592,13 +659,15 @@ __global__ void reset_counter_list(const __grid_constant__ CounterList l)
     }
 }
 
-template <int NT, int H, int TB, typename T, bool SIGNCHK = true>
+template <int NT, int H, int TB, typename T, bool SIGNCHK = true, bool BANDED = false>
 cudaError_t launch_one(const StagedLaunch &a, cudaStream_t s)
 {
     using C = Cfg<NT, H, TB, T>;
     Params<NT, H, T> p;
     std::memset(&p, 0, sizeof p);
     std::memcpy(p.maps, a.maps, sizeof(CUtensorMap) * H);
+    if constexpr (BANDED)
+        std::memcpy(p.split1, a.split1, sizeof(CUtensorMap) * 2);
     for (int g = 0; g < C::G; ++g)
         p.tmin[g] = a.tmin_host[g];
     p.ta = a.ta;
@@ -615,7 +684,7 @@ cudaError_t launch_one(const StagedLaunch &a, cudaStream_t s)
     p.n_slots = a.tile_hi - a.tile_lo;
     if (p.n_slots <= 0)
         return cudaSuccess;
-    auto kern = staged_kernel<NT, H, TB, T, SIGNCHK>;
+    auto kern = staged_kernel<NT, H, TB, T, SIGNCHK, BANDED>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e == cudaSuccess) // all of the unified L1/shared storage as shared memory
         e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -632,6 +701,19 @@ cudaError_t launch_one(const StagedLaunch &a, cudaStream_t s)
     }
     kern<<<grid, TB, C::SMEM, s>>>(p);
     return cudaGetLastError();
+}
+
+// A plane declared non-negative, one CTA per tile.  FP32 planes load level 1
+// in row bands (169 against 173 us on the 85 x 2^21 plane); 16-bit planes
+// keep one barrier (the banded form measured 2 us slower there).
+template <int NT, int H, int TB, typename T>
+cudaError_t launch_nonneg(const StagedLaunch &a, cudaStream_t s)
+{
+    if constexpr (sizeof(T) == 4) {
+        if (a.split1)
+            return launch_one<NT, H, TB, T, false, true>(a, s);
+    }
+    return launch_one<NT, H, TB, T, false>(a, s);
 }
 
 template <int NT, int H, int TB, int NC, int S, typename T>
@@ -888,7 +970,7 @@ cudaError_t launch_staged(const StagedLaunch &a, cudaStream_t s)
     if (a.assume_nonneg && a.grid_per_sm == 0) {
 #define X(NT_, H_, TB_, T_, DT_)                                                              \
         if (sh.nt == NT_ && sh.H == H_ && sh.tb == TB_ && sh.dtype == DT_)                   \
-            return launch_one<NT_, H_, TB_, T_, false>(a, s);
+            return launch_nonneg<NT_, H_, TB_, T_>(a, s);
         HS_NONNEG_SHAPES(X)
 #undef X
     }
