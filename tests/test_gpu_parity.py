@@ -134,6 +134,30 @@ def test_declared_nonnegative_planes_same_records(nt, n, H, dtype):
         assert_matches_oracle(b, ref, near)
 
 
+@pytest.mark.parametrize("nt,H", [(85, 16), (21, 8)])
+def test_level_one_band_edges(nt, H):
+    # FP32 planes declared non-negative load level 1 in row bands (rows
+    # |z| <= Z/2 with the first barrier, the outer rows with a second one the
+    # walk waits for at pair Z/2 + 1): peaks on both sides of the band edge
+    # and on the outermost rows, in a full tile and in the ragged last one,
+    # give the oracle's records
+    Z = (nt - 1) // 2
+    rb = Z // 2
+    n = 3000  # 23 full tiles of 128 bins and a ragged one
+    plane = synth.noise(nt, n, seed=61)
+    rows = [0, Z - rb - 1, Z - rb, Z + rb, Z + rb + 1, nt - 1]
+    for i, r in enumerate(rows):
+        plane[r, 100 + 37 * i] = 60.0
+        plane[r, n - 1 - i] = 60.0
+    ta = synth.thresholds(1e-8, H, nt)
+    recs, cnt, st, used = run_gpu(plane, H, ta, assume_nonneg=True)
+    assert used == "staged" and st == hs.HS_OK
+    ref, near = oracle.detect(plane, H, ta, threads=8)
+    assert_matches_oracle(recs, ref, near)
+    level1_rows = {int(r["z"]) + Z for r in recs if int(r["k"]) == 1}
+    assert set(rows) <= level1_rows
+
+
 def test_signed_inputs_take_the_exact_path():
     # Negative inputs void the monotone-sum prefilter; the staged kernel must
     # notice and test every level exactly.
