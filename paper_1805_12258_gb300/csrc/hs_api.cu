@@ -102,6 +102,26 @@ CUresult hs::encode_tensor_map(CUtensorMap *map, int dtype, const void *base, lo
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
 }
 
+CUresult hs::encode_plane_maps(const StagedShape &sh, const void *base, long long n_bins,
+                               long long ld, CUtensorMap *maps, CUtensorMap *split1)
+{
+    int w = 0, rows = 0;
+    for (int m = 1; m <= sh.H; ++m) {
+        staged_box(sh, m, &w, &rows);
+        const CUresult r =
+            encode_tensor_map(&maps[m - 1], sh.dtype, base, n_bins, ld, sh.nt, w, rows);
+        if (r != CUDA_SUCCESS)
+            return r;
+    }
+    staged_box(sh, 1, &w, &rows);
+    const int z = (sh.nt - 1) / 2, rb = z / 2;
+    const CUresult r =
+        encode_tensor_map(&split1[0], sh.dtype, base, n_bins, ld, sh.nt, w, 2 * rb + 1);
+    if (r != CUDA_SUCCESS)
+        return r;
+    return encode_tensor_map(&split1[1], sh.dtype, base, n_bins, ld, sh.nt, w, z - rb);
+}
+
 int hs::group_bounds(const float *ta, int n_templates, int H, float delta, float band_abs,
                      float *out)
 {
@@ -189,30 +209,12 @@ hs_status encode_maps(hs_plan *p, const void *fop)
     if (p->map_ptr == fop)
         return HS_OK;
     const StagedShape sh{p->nt, p->H, p->tb, p->opt.dtype};
-    for (int m = 1; m <= p->H; ++m) {
-        int w = 0, rows = 0;
-        staged_box(sh, m, &w, &rows);
-        CUresult r = encode_tensor_map(&p->maps[m - 1], p->opt.dtype, fop, p->n, p->ld, p->nt, w, rows);
-        if (r != CUDA_SUCCESS) {
-            p->map_ptr = nullptr;
-            char buf[128];
-            std::snprintf(buf, sizeof buf, "cuTensorMapEncodeTiled failed (%d) for m=%d", (int)r, m);
-            return fail(HS_ERR_CUDA, buf);
-        }
-    }
-    {
-        // level 1 in bands: rows [Z - Z/2, Z + Z/2] and Z - Z/2 rows per side
-        int w = 0, rows = 0;
-        staged_box(sh, 1, &w, &rows);
-        const int z = (p->nt - 1) / 2, rb = z / 2;
-        CUresult r = encode_tensor_map(&p->split1[0], p->opt.dtype, fop, p->n, p->ld, p->nt, w,
-                                       2 * rb + 1);
-        if (r == CUDA_SUCCESS)
-            r = encode_tensor_map(&p->split1[1], p->opt.dtype, fop, p->n, p->ld, p->nt, w, z - rb);
-        if (r != CUDA_SUCCESS) {
-            p->map_ptr = nullptr;
-            return fail(HS_ERR_CUDA, "cuTensorMapEncodeTiled failed for the level-1 bands");
-        }
+    const CUresult r = encode_plane_maps(sh, fop, p->n, p->ld, p->maps, p->split1);
+    if (r != CUDA_SUCCESS) {
+        p->map_ptr = nullptr;
+        char buf[96];
+        std::snprintf(buf, sizeof buf, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return fail(HS_ERR_CUDA, buf);
     }
     p->map_ptr = fop;
     return HS_OK;

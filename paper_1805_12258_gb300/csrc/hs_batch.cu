@@ -229,15 +229,8 @@ hs_status hs_batch_set_beams(hs_batch *b, const hs_beam *beams, int n_beams, hs_
             return fail(HS_ERR_INVALID, "beam " + std::to_string(i) + ": bad FP32 copy");
         StagedBatchBeam &d = nb[(size_t)i];
         std::memset(&d, 0, sizeof d);
-        for (int m = 1; m <= b->H; ++m) {
-            int w = 0, rows = 0;
-            staged_box(sh, m, &w, &rows);
-            CUresult r = encode_tensor_map(&d.maps[m - 1], b->dtype, bm.fop, bm.n_bins, ld, b->nt,
-                                           w, rows);
-            if (r != CUDA_SUCCESS)
-                return fail(HS_ERR_CUDA, "cuTensorMapEncodeTiled failed for beam " +
-                                             std::to_string(i));
-        }
+        if (encode_plane_maps(sh, bm.fop, bm.n_bins, ld, d.maps, d.split1) != CUDA_SUCCESS)
+            return fail(HS_ERR_CUDA, "cuTensorMapEncodeTiled failed for beam " + std::to_string(i));
         d.fop32 = bm.fop32;
         d.n = bm.n_bins;
         d.ld = ld;

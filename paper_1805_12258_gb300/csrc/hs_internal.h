@@ -87,6 +87,7 @@ cudaError_t launch_staged(const StagedLaunch &a, cudaStream_t s);
 // as many launches as the beam count needs.
 struct StagedBatchBeam {
     CUtensorMap maps[kMaxStagedH]; // host copies, H descriptors
+    CUtensorMap split1[2];         // level 1 in row bands (centre, outer side)
     const float *fop32;
     long long n, ld;
     hs_cand *rec;
@@ -124,6 +125,11 @@ hs_status batch_set_prepared(hs_batch *b, const StagedBatchBeam *beams, int n_be
 std::vector<uint32_t> tile_order(int n_tiles, int kind);
 CUresult encode_tensor_map(CUtensorMap *map, int dtype, const void *base, long long n_bins,
                            long long ld, int n_templates, int box_w, int box_rows);
+// The staged kernel's descriptors of one plane [sh.nt][n_bins] (row pitch
+// ld): the H span boxes, then level 1 in row bands (centre rows
+// [Z - Z/2, Z + Z/2], and Z - Z/2 rows for one outer side).
+CUresult encode_plane_maps(const StagedShape &sh, const void *base, long long n_bins,
+                           long long ld, CUtensorMap *maps, CUtensorMap *split1);
 // Prefilter bound of each level group: the smallest threshold of the group
 // over all rows, lowered for 16-bit storage error and for the fast pass's
 // summation order.  Returns the number of groups.

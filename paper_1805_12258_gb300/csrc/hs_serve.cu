@@ -291,13 +291,8 @@ void launch_group(hs_server *s, Group &g)
             std::memset(&d, 0, sizeof d);
             const long long ld = r.r.ld ? r.r.ld : n;
             const StagedShape sh{nt, s->cfg.H, 128, r.r.dtype};
-            for (int m = 1; m <= s->cfg.H && st == HS_OK; ++m) {
-                int w = 0, rows = 0;
-                staged_box(sh, m, &w, &rows);
-                if (encode_tensor_map(&d.maps[m - 1], r.r.dtype, r.r.fop, n, ld, nt, w, rows) !=
-                    CUDA_SUCCESS)
-                    st = fail(HS_ERR_CUDA, "cuTensorMapEncodeTiled failed for a resident plane");
-            }
+            if (encode_plane_maps(sh, r.r.fop, n, ld, d.maps, d.split1) != CUDA_SUCCESS)
+                st = fail(HS_ERR_CUDA, "cuTensorMapEncodeTiled failed for a resident plane");
             d.fop32 = lowp ? r.r.fop32 : nullptr;
             d.ld = ld;
         } else {
@@ -545,14 +540,10 @@ hs_status hs_server_create(hs_server **out, const hs_server_config *cfg)
             std::memset(&b, 0, sizeof b);
             const void *base = d == 0 ? (const void *)(s->d_f32 + (size_t)i * c.n_templates * s->ld_max)
                                       : (const void *)(s->d_bf + (size_t)i * c.n_templates * s->ld_max);
-            for (int m = 1; m <= c.H; ++m) {
-                int w = 0, rows = 0;
-                staged_box(d == 0 ? sh32 : sh16, m, &w, &rows);
-                if (encode_tensor_map(&b.maps[m - 1], d == 0 ? HS_F32 : HS_BF16, base, s->ld_max,
-                                      s->ld_max, c.n_templates, w, rows) != CUDA_SUCCESS) {
-                    free_server(s);
-                    return fail(HS_ERR_CUDA, "cuTensorMapEncodeTiled failed for a slot");
-                }
+            if (encode_plane_maps(d == 0 ? sh32 : sh16, base, s->ld_max, s->ld_max, b.maps,
+                                  b.split1) != CUDA_SUCCESS) {
+                free_server(s);
+                return fail(HS_ERR_CUDA, "cuTensorMapEncodeTiled failed for a slot");
             }
         }
     for (int i = c.n_slots - 1; i >= 0; --i)

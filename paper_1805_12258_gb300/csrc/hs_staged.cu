@@ -575,6 +575,7 @@ __global__ void __launch_bounds__(NC *TB + 32, 1)
 template <int H>
 struct BeamParam {
     CUtensorMap maps[H];
+    CUtensorMap split1[2]; // level 1 in row bands (centre, outer side)
     const float *fop32;
     long long n;
     long long ld;
@@ -609,16 +610,20 @@ struct BatchParams {
 // walk the concatenated tiles of the launch's beams grid-stride (one tile per
 // CTA when the grid covers them) and find each tile's beam by a CTA-uniform
 // scan of the cumulative tile ends.
-template <int NT, int H, int TB, typename T, bool SIGNCHK = true>
+template <int NT, int H, int TB, typename T, bool SIGNCHK = true, bool BANDED = false>
 __global__ void __launch_bounds__(TB, (resident_ctas<NT, H, TB, T>()))
     batched_kernel(const __grid_constant__ BatchParams<NT, H, T> p)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar_storage;
+    __shared__ __align__(8) uint64_t bar_storage[2];
     const uint32_t sbase = smem_addr(smem);
-    const uint32_t bar = smem_addr(&bar_storage);
-    if (threadIdx.x == 0)
+    const uint32_t bar = smem_addr(&bar_storage[0]);
+    const uint32_t bar_out = smem_addr(&bar_storage[1]);
+    if (threadIdx.x == 0) {
         mbar_init(bar, 1);
+        if constexpr (BANDED)
+            mbar_init(bar_out, 1);
+    }
     __syncthreads();
     int cur = -1; // beam whose descriptors thread 0 last prefetched
     uint32_t parity = 0;
@@ -629,15 +634,24 @@ __global__ void __launch_bounds__(TB, (resident_ctas<NT, H, TB, T>()))
         const BeamParam<H> &bp = p.beam[b];
         const int local = i - (b ? p.beam[b - 1].tile_end : 0);
         const int tile = p.order ? (int)__ldg(p.order + p.slot_base + i) : local;
-        const TileTarget tt{bp.maps, nullptr, bp.fop32, bp.n, bp.ld, bp.rec, bp.counters, bp.cap};
+        const TileTarget tt{bp.maps, bp.split1, bp.fop32, bp.n, bp.ld, bp.rec, bp.counters,
+                            bp.cap};
         if (threadIdx.x == 0) {
-            if (b != cur)
+            if (b != cur) {
                 static_for<0, H>([&](auto M) { prefetch_tmap(&bp.maps[M]); });
-            issue_tile<NT, H, TB, T>(tt, tile * TB, sbase, bar);
+                if constexpr (BANDED) {
+                    prefetch_tmap(&bp.split1[0]);
+                    prefetch_tmap(&bp.split1[1]);
+                }
+            }
+            if constexpr (BANDED)
+                issue_tile_banded<NT, H, TB, T>(tt, tile * TB, sbase, bar, bar_out);
+            else
+                issue_tile<NT, H, TB, T>(tt, tile * TB, sbase, bar);
         }
         cur = b;
-        if (!sum_tile<NT, H, TB, T, BatchParams<NT, H, T>, CtaOr, SIGNCHK>(p, tt, tile * TB,
-                                                                           smem, bar, parity))
+        if (!sum_tile<NT, H, TB, T, BatchParams<NT, H, T>, CtaOr, SIGNCHK, BANDED>(
+                p, tt, tile * TB, smem, bar, parity, CtaOr{}, bar_out))
             break;
         __syncthreads();
     }
@@ -757,7 +771,7 @@ cudaError_t launch_pipe(const StagedLaunch &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <int NT, int H, int TB, typename T, bool SIGNCHK = true>
+template <int NT, int H, int TB, typename T, bool SIGNCHK = true, bool BANDED = false>
 cudaError_t launch_batch_one(const StagedBatch &a, cudaStream_t s)
 {
     using C = Cfg<NT, H, TB, T>;
@@ -774,7 +788,7 @@ cudaError_t launch_batch_one(const StagedBatch &a, cudaStream_t s)
     }
     if (e != cudaSuccess)
         return e;
-    auto kern = batched_kernel<NT, H, TB, T, SIGNCHK>;
+    auto kern = batched_kernel<NT, H, TB, T, SIGNCHK, BANDED>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -797,6 +811,7 @@ cudaError_t launch_batch_one(const StagedBatch &a, cudaStream_t s)
             const StagedBatchBeam &src = a.beams[b0 + j];
             BeamParam<H> &d = p.beam[j];
             std::memcpy(d.maps, src.maps, sizeof(CUtensorMap) * H);
+            std::memcpy(d.split1, src.split1, sizeof(CUtensorMap) * 2);
             d.fop32 = src.fop32;
             d.n = src.n;
             d.ld = src.ld;
@@ -922,7 +937,7 @@ cudaError_t launch_staged_batch(const StagedBatch &a, cudaStream_t s)
     if (a.assume_nonneg) {
 #define X(NT_, H_, TB_, T_, DT_)                                                              \
         if (sh.nt == NT_ && sh.H == H_ && sh.tb == TB_ && sh.dtype == DT_)                   \
-            return launch_batch_one<NT_, H_, TB_, T_, false>(a, s);
+            return launch_batch_one<NT_, H_, TB_, T_, false, sizeof(T_) == 4>(a, s);
         HS_BATCH_SHAPES(X)
 #undef X
     }
