@@ -431,6 +431,27 @@ HS_API hs_status hs_postfilter(const hs_cand *in, uint32_t n, int policy, uint32
                                hs_cand *out, uint32_t *n_out);
 HS_API const char *hs_postfilter_last_error(void);
 
+/* Host logic of the staged kernel, exposed for inspection and tests (no GPU
+ * needed).
+ *
+ * hs_prefilter_bounds: the fast pass's bound of each level group (Eq. 2 sums
+ * tested at the group ends 2, 4, 8, then every 4 levels, and H): the smallest
+ * threshold TA(k, row) of the group's levels over all rows, lowered by the
+ * storage error of dtype (BF16, FP16: relative error of the stored values,
+ * plus the FP16 subnormal spacing) and by the rounding of the fast pass's
+ * FP32 sums, so that the prefilter never drops a point whose FP32 level sum
+ * (ascending m, Eq. 2 order) exceeds its threshold.  thresholds: host
+ * [H][n_templates] float32.  ends[8] receives the last level of each group,
+ * bounds[8] its bound, *n_groups the group count.  Errors: HS_ERR_INVALID
+ * (null pointers, n_templates not odd in 1..127, H not in 2..16).
+ *
+ * hs_tile_order: the order in which a plan visits the tiles of a plane
+ * (hs_options.order; 0 = the default), as tile indices: out[n_tiles] is a
+ * permutation of 0 .. n_tiles-1.  Errors: HS_ERR_INVALID. */
+HS_API hs_status hs_prefilter_bounds(const float *thresholds, int n_templates, int H, int dtype,
+                                     int *ends, float *bounds, int *n_groups);
+HS_API hs_status hs_tile_order(int n_tiles, int order, uint32_t *out);
+
 HS_API const char *hs_status_str(hs_status s);
 HS_API const char *hs_last_error(void);
 

@@ -122,6 +122,18 @@ CUresult hs::encode_plane_maps(const StagedShape &sh, const void *base, long lon
     return encode_tensor_map(&split1[1], sh.dtype, base, n_bins, ld, sh.nt, w, z - rb);
 }
 
+void hs::storage_error(int dtype, int H, float *delta, float *band_abs)
+{
+    *delta = 0.f;
+    *band_abs = 0.f;
+    if (dtype == HS_BF16) {
+        *delta = (float)((std::ldexp(1.0, -8) + H * std::ldexp(1.0, -22)) * 1.01);
+    } else if (dtype == HS_F16) {
+        *delta = (float)((std::ldexp(1.0, -11) + H * std::ldexp(1.0, -22)) * 1.01);
+        *band_abs = (float)(H * std::ldexp(1.0, -24));
+    }
+}
+
 int hs::group_bounds(const float *ta, int n_templates, int H, float delta, float band_abs,
                      float *out)
 {
@@ -317,6 +329,32 @@ hs_status launch_range(hs_plan *p, const void *fop, const float *fop32, cudaStre
 
 extern "C" {
 
+
+hs_status hs_prefilter_bounds(const float *thresholds, int n_templates, int H, int dtype,
+                              int *ends, float *bounds, int *n_groups)
+{
+    if (!thresholds || !ends || !bounds || !n_groups)
+        return fail(HS_ERR_INVALID, "null pointer");
+    if (n_templates < 1 || n_templates > 127 || n_templates % 2 == 0 || H < 2 ||
+        H > kMaxStagedH || dtype < HS_F32 || dtype > HS_F16)
+        return fail(HS_ERR_INVALID, "n_templates must be odd in 1..127, H in 2..16");
+    float delta = 0.f, band_abs = 0.f;
+    storage_error(dtype, H, &delta, &band_abs);
+    const int g = staged_groups(H, ends);
+    group_bounds(thresholds, n_templates, H, delta, band_abs, bounds);
+    *n_groups = g;
+    return HS_OK;
+}
+
+hs_status hs_tile_order(int n_tiles, int order, uint32_t *out)
+{
+    if (n_tiles < 0 || (n_tiles > 0 && !out) || order < 0 || order > 3)
+        return fail(HS_ERR_INVALID, "n_tiles >= 0, order in 0..3 and an output array");
+    const std::vector<uint32_t> o = tile_order(n_tiles, order == 0 ? 3 : order);
+    std::copy(o.begin(), o.end(), out);
+    return HS_OK;
+}
+
 const char *hs_status_str(hs_status s)
 {
     switch (s) {
@@ -375,12 +413,7 @@ hs_status hs_plan_create(hs_plan **out, int n_templates, int64_t n_bins, int H,
     p->opt = o;
     cudaGetDevice(&p->device);
     p->ta.assign(thresholds, thresholds + (size_t)H * n_templates);
-    if (o.dtype == HS_BF16)
-        p->delta = (float)((std::ldexp(1.0, -8) + H * std::ldexp(1.0, -22)) * 1.01);
-    else if (o.dtype == HS_F16) {
-        p->delta = (float)((std::ldexp(1.0, -11) + H * std::ldexp(1.0, -22)) * 1.01);
-        p->band_abs = (float)(H * std::ldexp(1.0, -24));
-    }
+    storage_error(o.dtype, H, &p->delta, &p->band_abs);
 
     // kernel choice: the staged kernel needs a compiled shape, the paper's
     // index map with symmetric rounding, and 16-byte aligned rows for TMA

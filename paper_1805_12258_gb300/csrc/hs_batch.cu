@@ -115,12 +115,7 @@ hs_status hs_batch_create(hs_batch **out, int n_templates, int H, const float *t
     b->assume_nonneg = o.assume_nonneg != 0;
     b->max_beams = max_beams;
     b->ta.assign(thresholds, thresholds + (size_t)H * n_templates);
-    if (o.dtype == HS_BF16)
-        b->delta = (float)((std::ldexp(1.0, -8) + H * std::ldexp(1.0, -22)) * 1.01);
-    else if (o.dtype == HS_F16) {
-        b->delta = (float)((std::ldexp(1.0, -11) + H * std::ldexp(1.0, -22)) * 1.01);
-        b->band_abs = (float)(H * std::ldexp(1.0, -24));
-    }
+    storage_error(b->dtype, H, &b->delta, &b->band_abs);
     group_bounds(b->ta.data(), n_templates, H, b->delta, b->band_abs, b->tmin);
     int dev = 0;
     cudaGetDevice(&dev);

@@ -130,6 +130,10 @@ CUresult encode_tensor_map(CUtensorMap *map, int dtype, const void *base, long l
 // [Z - Z/2, Z + Z/2], and Z - Z/2 rows for one outer side).
 CUresult encode_plane_maps(const StagedShape &sh, const void *base, long long n_bins,
                            long long ld, CUtensorMap *maps, CUtensorMap *split1);
+// Error bounds of 16-bit storage for H levels: the relative error of a
+// stored value's sum (*delta) and the absolute one of FP16 subnormals
+// (*band_abs); both 0 for FP32.
+void storage_error(int dtype, int H, float *delta, float *band_abs);
 // Prefilter bound of each level group: the smallest threshold of the group
 // over all rows, lowered for 16-bit storage error and for the fast pass's
 // summation order.  Returns the number of groups.

@@ -165,6 +165,10 @@ def lib():
     L.hs_postfilter.restype = i32
     L.hs_postfilter_last_error.argtypes = []
     L.hs_postfilter_last_error.restype = ctypes.c_char_p
+    L.hs_prefilter_bounds.argtypes = [vp, i32, i32, i32, P(i32), P(ctypes.c_float), P(i32)]
+    L.hs_prefilter_bounds.restype = i32
+    L.hs_tile_order.argtypes = [i32, i32, vp]
+    L.hs_tile_order.restype = i32
     L.hs_selftest_wait_timeout.argtypes = [vp, ctypes.c_uint64, vp]
     L.hs_selftest_wait_timeout.restype = i32
     L.hs_run_range.argtypes = [vp, vp, vp, i64, i64, vp, P(hs_cand_buf), i32]
@@ -296,6 +300,27 @@ def hs_plan_kernel_time(plan):
     _check(lib().hs_plan_kernel_time(plan, ctypes.byref(ms), ctypes.byref(n)),
            "hs_plan_kernel_time")
     return ms.value, n.value
+
+
+def hs_prefilter_bounds(thresholds, dtype="f32"):
+    """(ends, bounds): the staged kernel's level groups (last level of each)
+    and their prefilter bounds for thresholds [H][n_templates]."""
+    ta = np.ascontiguousarray(thresholds, dtype=np.float32)
+    H, nt = ta.shape
+    ends = (ctypes.c_int * 8)()
+    bounds = (ctypes.c_float * 8)()
+    ng = ctypes.c_int(0)
+    _check(lib().hs_prefilter_bounds(ta.ctypes.data, nt, H, DTYPES[dtype], ends, bounds,
+                                     ctypes.byref(ng)), "hs_prefilter_bounds")
+    g = ng.value
+    return (np.array(ends[:g], dtype=np.int32), np.array(bounds[:g], dtype=np.float32))
+
+
+def hs_tile_order(n_tiles, order=0):
+    """The tile indices of a plane in the order a plan visits them."""
+    out = np.zeros(max(1, int(n_tiles)), dtype=np.uint32)
+    _check(lib().hs_tile_order(int(n_tiles), int(order), out.ctypes.data), "hs_tile_order")
+    return out[:int(n_tiles)]
 
 
 def hs_status_str(s):
