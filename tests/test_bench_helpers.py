@@ -1,0 +1,72 @@
+"""Measurement plumbing on the CPU: the kernel source hash that ties a
+committed ncu summary to the code it was taken on, the traffic lookup that
+bench.py reports from it, and the autotuner's result cache."""
+import json
+import os
+import shutil
+
+import pytest
+
+import bench
+from paper_1805_12258_gb300 import autotune
+
+CSRC = os.path.join("paper_1805_12258_gb300", "csrc")
+
+
+def _copy_sources(root):
+    os.makedirs(os.path.join(root, CSRC))
+    for f in ("hs_staged.cu", "hs_device.cuh"):
+        shutil.copy(os.path.join(bench.ROOT, CSRC, f), os.path.join(root, CSRC, f))
+
+
+def test_hash_ignores_comments_and_spacing(tmp_path, monkeypatch):
+    _copy_sources(tmp_path)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.kernel_source_hash()
+    path = os.path.join(tmp_path, CSRC, "hs_staged.cu")
+    src = open(path).read()
+    open(path, "w").write("// a new comment\n/* and a block\n comment */\n" +
+                          src.replace("\n", "\n\n", 3))
+    assert bench.kernel_source_hash() == h0
+    open(path, "w").write(src + "\nint x;\n")
+    assert bench.kernel_source_hash() != h0
+
+
+def test_traffic_only_for_the_profiled_source(tmp_path, monkeypatch):
+    # the committed table names the kernel by shape, type, tile and order
+    key = "staged 85x2097152 H=16 f32 tb=128 order=semitone"
+    t = bench.profiled_traffic(key)
+    assert t is not None and 700e6 < t < 900e6  # the 713 MB plane and its re-reads
+    assert bench.profiled_traffic(key.replace("semitone", "octave")) is None
+    # a changed kernel source voids the figure
+    _copy_sources(tmp_path)
+    os.makedirs(os.path.join(tmp_path, "profiles"))
+    shutil.copy(os.path.join(bench.ROOT, "profiles", "traffic.txt"),
+                os.path.join(tmp_path, "profiles", "traffic.txt"))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.profiled_traffic(key) == t
+    path = os.path.join(tmp_path, CSRC, "hs_device.cuh")
+    open(path, "a").write("\nstatic int changed;\n")
+    assert bench.profiled_traffic(key) is None
+
+
+def test_order_names():
+    assert bench.ORDER_NAMES[0] == bench.ORDER_NAMES[3] == "semitone"
+    assert bench.ORDER_NAMES[1] == "linear" and bench.ORDER_NAMES[2] == "octave"
+
+
+def test_tune_cache_round_trip(tmp_path, monkeypatch):
+    path = tmp_path / "sub" / "tune.json"
+    monkeypatch.setenv("HS_TUNE_CACHE", str(path))
+    assert autotune.cache_path() == str(path)
+    assert autotune._load() == {}
+    k = autotune.key_of("plane", 85, 16, "f32", 2 ** 21)
+    assert k == "plane:85x16:f32:2^21"
+    # bin counts are classed by the nearest power of two
+    assert autotune.key_of("plane", 85, 16, "f32", 3_000_000) == "plane:85x16:f32:2^22"
+    autotune._store(k, {"best": {"tile_bins": 128}, "table": []})
+    autotune._store("other", {"best": {}, "table": []})
+    d = json.loads(path.read_text())
+    assert d[k]["best"] == {"tile_bins": 128} and "other" in d
+    path.write_text("{ not json")
+    assert autotune._load() == {}
