@@ -33,21 +33,34 @@ def test_hash_ignores_comments_and_spacing(tmp_path, monkeypatch):
 
 
 def test_traffic_only_for_the_profiled_source(tmp_path, monkeypatch):
-    # the committed table names the kernel by shape, type, tile and order
-    key = "staged 85x2097152 H=16 f32 tb=128 order=semitone"
-    t = bench.profiled_traffic(key)
-    assert t is not None and 700e6 < t < 900e6  # the 713 MB plane and its re-reads
-    assert bench.profiled_traffic(key.replace("semitone", "octave")) is None
-    # a changed kernel source voids the figure
+    # a table entry counts only for its kernel name and the source hash it
+    # was taken on; any later change of the kernel's code voids it
     _copy_sources(tmp_path)
-    os.makedirs(os.path.join(tmp_path, "profiles"))
-    shutil.copy(os.path.join(bench.ROOT, "profiles", "traffic.txt"),
-                os.path.join(tmp_path, "profiles", "traffic.txt"))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.profiled_traffic(key) == t
+    sha = bench.kernel_source_hash()
+    key = "staged 85x2097152 H=16 f32 tb=128 order=semitone"
+    os.makedirs(os.path.join(tmp_path, "profiles"))
+    with open(os.path.join(tmp_path, "profiles", "traffic.txt"), "w") as fh:
+        fh.write("# kernel | dram_bytes_per_launch | kernel_sha | summary\n")
+        fh.write(f"{key} | 765780224 | {sha} | x.md\n")
+        fh.write(f"{key.replace('f32', 'bf16')} | 368234496 | 0123456789abcdef | y.md\n")
+    assert bench.profiled_traffic(key) == 765780224
+    assert bench.profiled_traffic(key.replace("semitone", "octave")) is None
+    assert bench.profiled_traffic(key.replace("f32", "bf16")) is None  # other source
     path = os.path.join(tmp_path, CSRC, "hs_device.cuh")
     open(path, "a").write("\nstatic int changed;\n")
     assert bench.profiled_traffic(key) is None
+
+
+def test_committed_traffic_table_is_well_formed():
+    with open(os.path.join(bench.ROOT, "profiles", "traffic.txt")) as fh:
+        rows = [ln.split("|") for ln in fh if ln.strip() and not ln.startswith("#")]
+    assert rows
+    for r in rows:
+        name, traffic, sha, summary = (x.strip() for x in r)
+        assert name.startswith(("staged ", "generic ")) and int(traffic) > 0
+        assert len(sha) == 16 and int(sha, 16) >= 0
+        assert os.path.exists(os.path.join(bench.ROOT, "profiles", summary))
 
 
 def test_order_names():
