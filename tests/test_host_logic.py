@@ -17,7 +17,13 @@ import math
 import numpy as np
 import pytest
 
+from paper_1805_12258_gb300 import build as hsbuild
 from paper_1805_12258_gb300 import hs, synth
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _library():
+    hsbuild.build()  # no-op when libhs.so is up to date
 
 
 def group_ranges(ends):
