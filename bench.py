@@ -167,13 +167,34 @@ def oracle_sample(plane, ta, H, cpu_seconds, threads):
     bins = max(min(n, threads * 64), min(bins, n))
     lo = n - bins
     t0 = time.perf_counter()
-    cands, _ = oracle.detect(plane, H, ta, f_lo=lo, f_hi=n, threads=threads)
+    cands, near = oracle.detect(plane, H, ta, f_lo=lo, f_hi=n, threads=threads)
     dt = time.perf_counter() - t0
     what = "the whole plane" if bins == n else f"bins [{lo}, {n}) of the same plane"
     return {"value": nt * bins / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"all {nt} rows x {what} ({nt * bins} points, {H} levels, FP64), "
                       f"{threads} threads",
-            "seconds": dt, "candidates_in_sample": int(len(cands))}
+            "seconds": dt, "candidates_in_sample": int(len(cands)),
+            "_window": (lo, n), "_records": cands, "_near": near}
+
+
+def window_parity(gpu_records, cpu, rtol=1e-6):
+    """The GPU run's records with bins inside the oracle sample's window
+    against the oracle's records there: same (k, z, bin) set except points
+    the oracle lists within 1e-5 of their threshold, powers within rtol."""
+    lo, hi = cpu["_window"]
+    r = gpu_records[(gpu_records["bin"] >= lo) & (gpu_records["bin"] < hi)]
+    g = {(int(x["k"]), int(x["z"]), int(x["bin"])): float(x["power"]) for x in r}
+    o = {(int(c["k"]), int(c["z"]), int(c["f"])): float(c["power"]) for c in cpu["_records"]}
+    near = {(int(c["k"]), int(c["z"]), int(c["f"])) for c in cpu["_near"]}
+    only_gpu = set(g) - set(o) - near
+    only_oracle = set(o) - set(g) - near
+    common = set(g) & set(o)
+    err = max((abs(g[k] - o[k]) / max(abs(o[k]), 1e-30) for k in common), default=0.0)
+    return {"window_bins": [int(lo), int(hi)], "gpu_records": len(r),
+            "oracle_records": len(o), "near_threshold_excluded": len(near),
+            "only_gpu": len(only_gpu), "only_oracle": len(only_oracle),
+            "duplicates": len(r) - len(g), "max_rel_err": err, "rtol": rtol,
+            "equal": (not only_gpu and not only_oracle and len(r) == len(g) and err <= rtol)}
 
 
 def host_cores():
@@ -377,12 +398,13 @@ def run_ours(args):
         dist.barrier()
     elapsed_ms = float(t.item())
     st, n_cand = cands.sync(stream)
+    timed_records = cands.fetch(stream)[0]  # the last timed launch's records
 
     precision = None
     if args.dtype != "f32":
         # candidate set of the 16-bit plane (with FP32 rechecks) against the
         # FP32 path on the FP32 copy: equal record for record by design
-        low = cands.fetch(stream)[0]
+        low = timed_records
         c32 = hs.CandBuffer(1 << 20)
         with hs.Plan(nt, n, H, ta, index=args.index, kernel=args.kernel) as p32:
             p32.run(fop32, c32, stream)
@@ -435,9 +457,12 @@ def run_ours(args):
             e2e["recheck"] = "FP32 copy read in place from page-locked host memory"
         del dev
 
-    cpu = None
+    cpu, parity = None, None
     if rank == 0 and not args.no_cpu:
         cpu = oracle_sample(plane_np, ta, H, args.cpu_seconds, host_cores())
+        if not band and args.index == "stretch":
+            parity = window_parity(timed_records, cpu)
+        cpu = {k: v for k, v in cpu.items() if not k.startswith("_")}
 
     if rank == 0:
         line = {
@@ -472,7 +497,9 @@ def run_ours(args):
                          "mean_kernel_us": mean_kernel_s * 1e6,
                          "frac_of_8tbs": algo_bytes / mean_kernel_s / 8e12},
             "precision": precision,
-        "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
+            "parity_in_window": None if parity is None else parity["equal"],
+            "parity_window": parity,
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": launches_before, "status": hs.hs_status_str(st),
         }
         print(json.dumps(line), flush=True)

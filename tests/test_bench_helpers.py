@@ -83,3 +83,30 @@ def test_tune_cache_round_trip(tmp_path, monkeypatch):
     assert d[k]["best"] == {"tile_bins": 128} and "other" in d
     path.write_text("{ not json")
     assert autotune._load() == {}
+
+
+def test_window_parity_compares_records_inside_the_window():
+    import numpy as np
+
+    import oracle
+    from paper_1805_12258_gb300 import hs
+    o = np.zeros(3, oracle.CAND_DTYPE)
+    o["f"], o["z"], o["k"], o["power"] = [100, 150, 199], [0, -3, 5], [1, 4, 16], [20.0, 30.0, 50.0]
+    near = np.zeros(1, oracle.CAND_DTYPE)
+    near["f"], near["z"], near["k"], near["power"] = 160, 1, 2, 17.0
+    g = np.zeros(5, hs.CAND_DTYPE)
+    # three in-window records equal to the oracle's, one near-threshold
+    # record, one outside the window (bin 50)
+    g["bin"], g["z"], g["k"] = [100, 150, 199, 160, 50], [0, -3, 5, 1, 0], [1, 4, 16, 2, 1]
+    g["power"] = [20.0, 30.0, 50.0, 17.0, 99.0]
+    cpu = {"_window": (100, 200), "_records": o, "_near": near}
+    r = bench.window_parity(g, cpu)
+    assert r["equal"] and r["gpu_records"] == 4 and r["oracle_records"] == 3
+    g2 = g.copy()
+    g2["power"][1] = 30.0 * (1 + 3e-6)  # a power off by more than 1e-6
+    assert not bench.window_parity(g2, cpu)["equal"]
+    g3 = g[[0, 2, 3, 4]]  # a record missing
+    r3 = bench.window_parity(g3, cpu)
+    assert not r3["equal"] and r3["only_oracle"] == 1
+    g4 = np.concatenate([g, g[:1]])  # a duplicate record
+    assert not bench.window_parity(g4, cpu)["equal"]

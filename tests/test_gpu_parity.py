@@ -455,24 +455,51 @@ def ska():
     return wl, plane, ta
 
 
-def test_ska_plane_candidates(ska):
+@pytest.fixture(scope="module")
+def ska_oracle(ska):
     wl, plane, ta = ska
-    recs, n, st, used = run_gpu(plane, wl.H, ta)
+    return oracle.detect(plane, wl.H, ta, threads=16)
+
+
+# assume_nonneg=True is the launch configuration bench.py times (no sign
+# check, level 1 in row bands, semitone tile order); False the checked one.
+@pytest.mark.parametrize("assume_nonneg", [True, False])
+def test_ska_plane_candidates(ska, ska_oracle, assume_nonneg):
+    wl, plane, ta = ska
+    recs, n, st, used = run_gpu(plane, wl.H, ta, assume_nonneg=assume_nonneg)
     assert used == "staged" and st == hs.HS_OK
-    ref, near = oracle.detect(plane, wl.H, ta, threads=16)
+    ref, near = ska_oracle
+    assert n == len(recs) and n > 1000
     assert_matches_oracle(recs, ref, near)
 
 
-@pytest.mark.parametrize("z", [0, -42, 17])
-def test_ska_plane_row_sums(ska, z):
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+def test_ska_plane_lowp_recheck_candidates(ska, ska_oracle, dtype):
+    # Precision form at full size, in bench.py's launch configuration: the
+    # 16-bit plane with the FP32 copy for rechecks gives the FP64 oracle's
+    # candidate set on the FP32 plane (near-threshold points excepted)
+    wl, plane, ta = ska
+    low = _bf16_bits(plane) if dtype == "bf16" else plane.astype(np.float16)
+    recs, n, st, used = run_gpu(low, wl.H, ta, dtype=dtype, fop32=plane, assume_nonneg=True)
+    assert used == "staged" and st == hs.HS_OK
+    ref, near = ska_oracle
+    assert_matches_oracle(recs, ref, near)
+
+
+@pytest.mark.parametrize("z,assume_nonneg", [(0, True), (-42, True), (17, True), (42, True),
+                                             (-21, True), (22, True), (0, False), (-42, False),
+                                             (17, False)])
+def test_ska_plane_row_sums(ska, z, assume_nonneg):
     # Every level sum of one full row (2^21 bins x 16 levels), checked
     # against the oracle point by point: the row's thresholds are set below
-    # every value so each sum becomes a record.
+    # every value so each sum becomes a record.  Rows 21 / 22 straddle the
+    # edge of the level-1 centre band of the banded load.
     wl, plane, ta = ska
     Z = (wl.n_templates - 1) // 2
     ta2 = ta.copy()
     ta2[:, z + Z] = -1e30
-    recs, n, st, _ = run_gpu(plane, wl.H, ta2, cap=wl.n_bins * wl.H + (1 << 16))
+    recs, n, st, _ = run_gpu(plane, wl.H, ta2, cap=wl.n_bins * wl.H + (1 << 16),
+                             assume_nonneg=assume_nonneg)
     assert st == hs.HS_OK
     row = recs[recs["z"] == z]
     assert len(row) == wl.n_bins * wl.H
