@@ -24,7 +24,8 @@
 // group bound (a few values in registers; per-row bounds would have to be
 // re-read for every row and cost more than they save).  The fast pass forms
 // HP_b only at the group ends (each group summed as a tree with packed FP32
-// adds over the pair; each group's bound rides in the value of its first
+// adds over the pair, kept from pair to pair and re-added only where one of
+// its levels was reloaded; each group's bound rides in the value of its last
 // level, so a group's test is the sign of the running sum, the bounds lowered
 // by the FP32 error of that order) and marks the row pairs that might hold a
 // hit; the slow pass recomputes those rows
@@ -66,6 +67,15 @@ constexpr int group_index(int m, int H)
     return g;
 }
 constexpr int n_groups(int H) { return group_index(H, H) + 1; }
+// True when some level m in [lo, hi] changes its source row at pair zz >= 1
+// (m divides zz), i.e. when the walk reloads it there.
+constexpr bool reloads_any(int zz, int lo, int hi)
+{
+    for (int m = lo; m <= hi; ++m)
+        if (zz % m == 0)
+            return true;
+    return false;
+}
 
 template <int NT, int H, int TB, typename T>
 struct Cfg {
@@ -260,19 +270,20 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
     // exactly when HP_b < bound_g (IEEE addition is sign-exact without
     // flush-to-zero), so AND-ing the sign bits of every group's d leaves bit
     // 31 set iff no group of the pair can hold a hit.  The bounds ride along
-    // in the sums: the first level of group g carries c_g = bound_{g-1} -
-    // bound_g (c_0 = -bound_0) from the moment it is loaded, so the running
-    // sum over the groups is d_g itself and no separate subtraction is needed.
-    // The host lowers the bounds by the rounding this mixing of signs adds.
+    // in the sums: the last level of group g (the one reloaded least often)
+    // carries c_g = bound_{g-1} - bound_g (c_0 = -bound_0) from the moment it
+    // is loaded, so the running sum over the groups is d_g itself and no
+    // separate subtraction is needed.  The host lowers the bounds by the
+    // rounding this mixing of signs adds.
     float2 cg[C::G];
     static_for<0, C::G>([&](auto g) {
         const float c = g == 0 ? -p.tmin[0] : p.tmin[g - 1] - p.tmin[g];
         cg[g] = make_float2(c, c);
     });
-    // the group whose first level is m, or -1
-    auto first_of = [](int m) {
+    // the group whose last level is m, or -1
+    auto carrier_of = [](int m) {
         for (int g = 0; g < C::G; ++g)
-            if (C::GLO(g) == m)
+            if (C::GHI(g) == m)
                 return g;
         return -1;
     };
@@ -283,16 +294,34 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
     // 1) and turned into the mask once at the end.
     uint32_t clear[2] = {0u, 0u};
     float2 cur[H];
-    auto pair_test = [&]() -> uint32_t {
+    // Each group's tree sum, and the sums of its two halves, are kept from
+    // pair to pair and recomputed only at the pairs where one of their levels
+    // was reloaded (m divides zz), so the values are exactly those of a full
+    // recomputation of the tree.
+    float2 gsum[C::G], ghalf[C::G][2];
+    auto pair_test = [&](auto ZZ) -> uint32_t {
+        constexpr int zz = decltype(ZZ)::value;
         float2 acc = make_float2(0.f, 0.f);
         uint32_t sgn = 0xffffffffu;
         static_for<0, C::G>([&](auto g) {
-            constexpr int lo = C::GLO(g), hi = C::GHI(g);
-            const float2 gs = tree_sum<lo - 1, hi - 1>(cur);
+            constexpr int lo = C::GLO(g), hi = C::GHI(g), mid = (lo + hi) / 2;
+            if constexpr (lo == hi) {
+                if constexpr (zz == 0 || reloads_any(zz, lo, hi))
+                    gsum[g] = cur[lo - 1];
+            } else {
+                constexpr bool cl = zz == 0 || reloads_any(zz, lo, mid);
+                constexpr bool cr = zz == 0 || reloads_any(zz, mid + 1, hi);
+                if constexpr (cl)
+                    ghalf[g][0] = tree_sum<lo - 1, mid - 1>(cur);
+                if constexpr (cr)
+                    ghalf[g][1] = tree_sum<mid, hi - 1>(cur);
+                if constexpr (cl || cr)
+                    gsum[g] = __fadd2_rn(ghalf[g][0], ghalf[g][1]);
+            }
             if constexpr (g == 0)
-                acc = gs;
+                acc = gsum[g];
             else
-                acc = __fadd2_rn(acc, gs);
+                acc = __fadd2_rn(acc, gsum[g]);
             sgn &= __float_as_uint(acc.x) & __float_as_uint(acc.y);
         });
         return sgn; // bit 31 clear: the pair may hold a hit
@@ -303,7 +332,7 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
     };
     // the value of level m at the pair (tv, bv), with its group's bound share
     auto put = [&](auto M, float tv, float bv) {
-        constexpr int g = first_of(decltype(M)::value + 1);
+        constexpr int g = carrier_of(decltype(M)::value + 1);
         if constexpr (g >= 0)
             cur[M] = __fadd2_rn(make_float2(tv, bv), cg[g]);
         else
@@ -318,7 +347,7 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
             if constexpr (SIGNCHK)
                 negbits |= __float_as_uint(v);
         });
-        record(std::integral_constant<int, 0>{}, pair_test());
+        record(std::integral_constant<int, 0>{}, pair_test(std::integral_constant<int, 0>{}));
         // pairs (+zz, -zz): reload the value of m only when m divides zz
         static_for<1, Z + 1>([&](auto ZZ) {
             constexpr int zz = ZZ;
@@ -348,7 +377,7 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
                         negbits |= __float_as_uint(tv) | __float_as_uint(bv);
                 }
             });
-            record(ZZ, pair_test());
+            record(ZZ, pair_test(ZZ));
         });
         // word 0 holds pairs 0 .. n0-1 with pair zz at bit n0-1-zz, word 1
         // pairs 32 .. Z with pair zz at bit Z-zz; reverse the bits into the

@@ -6,7 +6,7 @@ and carries the bounds inside its FP32 sums.  It may mark too much, never too
 little: a point whose FP32 level sum (ascending m, the order of Eq. 2) exceeds
 its threshold must be marked.  These tests take the bounds the library
 computes (hs_prefilter_bounds), redo the fast pass's FP32 arithmetic in numpy
-in the kernel's order (each group's bound difference added to its first
+in the kernel's order (each group's bound difference added to its last
 level, each group summed as a pairwise tree, the groups chained), and check
 that promise on inputs built to sit within a few ulps above a threshold; for
 16-bit planes the fast pass sees the rounded values and the truth is the
@@ -51,9 +51,9 @@ def fast_pass_marks(v, ends, bounds):
     groups = group_ranges(ends)
     b = bounds.astype(np.float32)
     cur = v.copy()
-    for g, (lo, _) in enumerate(groups):
+    for g, (_, hi) in enumerate(groups):
         c = -b[0] if g == 0 else np.float32(b[g - 1] - b[g])
-        cur[:, lo - 1] = (cur[:, lo - 1] + c).astype(np.float32)
+        cur[:, hi - 1] = (cur[:, hi - 1] + c).astype(np.float32)
     marks = np.zeros((v.shape[0], len(groups)), bool)
     acc = None
     for g, (lo, hi) in enumerate(groups):
