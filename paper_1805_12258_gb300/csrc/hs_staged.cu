@@ -178,6 +178,34 @@ __device__ float chain_f32(const float *fop32, int Z, long long n, int z, int f,
     return s;
 }
 
+// The exact decision for level m of row z at bin f (Section III): s is the
+// level sum in Eq. 2 order (ascending m, FP32) of the stored values, a the
+// sum of their magnitudes.  FP32 planes (LOWP false): s > thr, and nothing
+// else is compiled in; the exact pass is rare, and its code, run cold from
+// the instruction cache, is what it costs.  16-bit planes with an FP32 copy:
+// a sum that could lie on either side of thr given the storage error is
+// re-added from the copy, and the copy's sum decides (and is the power);
+// without a copy the 16-bit sum decides and the record is flagged.
+template <bool LOWP>
+__device__ __forceinline__ bool level_hit(float s, float a, float thr, float delta,
+                                          float band_abs, const float *fop32, int Z,
+                                          long long ld, int z, int f, int m, float &power,
+                                          uint32_t &flags)
+{
+    power = s;
+    flags = 0u;
+    if (!LOWP || delta == 0.f)
+        return s > thr;
+    if (fop32 != nullptr) {
+        if (s == s && s + (delta * a + band_abs) < thr)
+            return false;
+        power = chain_f32(fop32, Z, ld, z, f, m);
+        return power > thr;
+    }
+    flags = HS_FLAG_LOWP | (fabsf(s - thr) <= delta * a + band_abs ? HS_FLAG_NEAR : 0u);
+    return s > thr;
+}
+
 // What one tile reads and writes: its plane's descriptors and size, and the
 // candidate buffer its hits go to (one plane for hs_run, a beam of a batch).
 struct TileTarget {
@@ -261,6 +289,43 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
         const int col = f / m - ((f0 / m) & ~(C::ALIGN - 1));
         bidx[M] = C::OFF(m) / C::ES + C::R(m) * C::W(m) + col;
     });
+
+    // ---- slow pass (defined here, run below): exact per-level test -----------
+    // scan(z, write, slot): level sums of row z in Eq. 2 order; returns the hit
+    // mask over levels and, when write is set, appends the records from slot.
+    auto scan = [&](int z, bool write, uint32_t rslot) -> uint32_t {
+        float acc = 0.f, ab = 0.f;
+        uint32_t hits = 0u;
+        float thr[H];
+        static_for<0, H>([&](auto M) { thr[M] = __ldg(p.ta + M * NT + (z + Z)); });
+        static_for<0, H>([&](auto M) {
+            constexpr int m = M + 1;
+            const int rho = z >= 0 ? z / m : -((-z) / m);
+            const float v = to_f32(sm[bidx[M] + rho * C::W(m)]);
+            acc = (m == 1) ? v : acc + v;
+            ab += fabsf(v);
+            float power;
+            uint32_t flags;
+            const bool hit = level_hit<(C::ES < 4)>(acc, ab, thr[M], p.delta, p.band_abs, tt.fop32,
+                                                  Z, tt.ld, z, f, m, power, flags);
+            if (hit) {
+                hits |= 1u << M;
+                if (write)
+                    put_record(tt.rec, rslot++, tt.cap, (uint32_t)f, z, m, flags, power);
+            }
+        });
+        return hits;
+    };
+
+    if constexpr (C::ES == 4) {
+        // FP32: a dry run of the exact pass on this thread's centre row while
+        // the copies are in flight (the values read are discarded): the
+        // pass's code is then in the instruction cache when a marked pair
+        // needs it.  (16-bit planes skip it: their pass may read the FP32
+        // copy, which a dry run has no business touching.)
+        const uint32_t dry = scan(0, false, 0u);
+        asm volatile("" ::"r"(dry));
+    }
 
     // CTA-uniform outcome of the bounded wait for the stage
     const bool ok = !any_of(!mbar_wait_bounded(bar, parity, kWaitLimitNs));
@@ -402,45 +467,6 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
         mask = 0ull;
     else if (negbits >> 31)
         mask = (Z == 63) ? ~0ull : ((1ull << (Z + 1)) - 1ull);
-
-    // ---- slow pass: exact per-level test of the marked row pairs --------------
-    // scan(z, write, slot): level sums of row z in Eq. 2 order; returns the hit
-    // mask over levels and, when write is set, appends the records from slot.
-    auto scan = [&](int z, bool write, uint32_t rslot) -> uint32_t {
-        float acc = 0.f, ab = 0.f;
-        uint32_t hits = 0u;
-        float thr[H];
-        static_for<0, H>([&](auto M) { thr[M] = __ldg(p.ta + M * NT + (z + Z)); });
-        static_for<0, H>([&](auto M) {
-            constexpr int m = M + 1;
-            const int rho = z >= 0 ? z / m : -((-z) / m);
-            const float v = to_f32(sm[bidx[M] + rho * C::W(m)]);
-            acc = (m == 1) ? v : acc + v;
-            ab += fabsf(v);
-            float power = acc;
-            uint32_t flags = 0u;
-            bool hit;
-            if (p.delta == 0.f) {
-                hit = acc > thr[M];
-            } else if (tt.fop32 != nullptr) {
-                hit = false;
-                if (!(acc == acc && acc + (p.delta * ab + p.band_abs) < thr[M])) {
-                    power = chain_f32(tt.fop32, Z, tt.ld, z, f, m);
-                    hit = power > thr[M];
-                }
-            } else {
-                hit = acc > thr[M];
-                flags = HS_FLAG_LOWP |
-                        (fabsf(acc - thr[M]) <= p.delta * ab + p.band_abs ? HS_FLAG_NEAR : 0u);
-            }
-            if (hit) {
-                hits |= 1u << M;
-                if (write)
-                    put_record(tt.rec, rslot++, tt.cap, (uint32_t)f, z, m, flags, power);
-            }
-        });
-        return hits;
-    };
 
     while (__any_sync(0xffffffffu, mask != 0ull)) {
         int zz = -1;
