@@ -165,47 +165,6 @@ __device__ __forceinline__ float2 tree_sum(const float2 (&cur)[N])
     }
 }
 
-// Level m value of the FP32 copy at (z, f): the Eq. 2 chain in FP32,
-// ascending m, i.e. exactly the number the FP32 path computes.
-__device__ float chain_f32(const float *fop32, int Z, long long n, int z, int f, int k)
-{
-    float s = 0.f;
-    for (int m = 1; m <= k; ++m) {
-        const int rho = z >= 0 ? z / m : -((-z) / m);
-        const float v = __ldg(fop32 + (long long)(rho + Z) * n + f / m);
-        s = (m == 1) ? v : s + v;
-    }
-    return s;
-}
-
-// The exact decision for level m of row z at bin f (Section III): s is the
-// level sum in Eq. 2 order (ascending m, FP32) of the stored values, a the
-// sum of their magnitudes.  FP32 planes (LOWP false): s > thr, and nothing
-// else is compiled in; the exact pass is rare, and its code, run cold from
-// the instruction cache, is what it costs.  16-bit planes with an FP32 copy:
-// a sum that could lie on either side of thr given the storage error is
-// re-added from the copy, and the copy's sum decides (and is the power);
-// without a copy the 16-bit sum decides and the record is flagged.
-template <bool LOWP>
-__device__ __forceinline__ bool level_hit(float s, float a, float thr, float delta,
-                                          float band_abs, const float *fop32, int Z,
-                                          long long ld, int z, int f, int m, float &power,
-                                          uint32_t &flags)
-{
-    power = s;
-    flags = 0u;
-    if (!LOWP || delta == 0.f)
-        return s > thr;
-    if (fop32 != nullptr) {
-        if (s == s && s + (delta * a + band_abs) < thr)
-            return false;
-        power = chain_f32(fop32, Z, ld, z, f, m);
-        return power > thr;
-    }
-    flags = HS_FLAG_LOWP | (fabsf(s - thr) <= delta * a + band_abs ? HS_FLAG_NEAR : 0u);
-    return s > thr;
-}
-
 // What one tile reads and writes: its plane's descriptors and size, and the
 // candidate buffer its hits go to (one plane for hs_run, a beam of a batch).
 struct TileTarget {
@@ -298,22 +257,73 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
         uint32_t hits = 0u;
         float thr[H];
         static_for<0, H>([&](auto M) { thr[M] = __ldg(p.ta + M * NT + (z + Z)); });
-        static_for<0, H>([&](auto M) {
-            constexpr int m = M + 1;
-            const int rho = z >= 0 ? z / m : -((-z) / m);
-            const float v = to_f32(sm[bidx[M] + rho * C::W(m)]);
-            acc = (m == 1) ? v : acc + v;
-            ab += fabsf(v);
-            float power;
-            uint32_t flags;
-            const bool hit = level_hit<(C::ES < 4)>(acc, ab, thr[M], p.delta, p.band_abs, tt.fop32,
-                                                  Z, tt.ld, z, f, m, power, flags);
-            if (hit) {
-                hits |= 1u << M;
-                if (write)
-                    put_record(tt.rec, rslot++, tt.cap, (uint32_t)f, z, m, flags, power);
+        // The decision of Section III: HP_k(z, f) > TA(k, z), HP_k formed in
+        // the order of Eq. 2 (ascending m) in FP32.  The pass is rare, so
+        // what it costs is its code run cold from the instruction cache; the
+        // FP32 form compiles nothing else.
+        if constexpr (C::ES == 4) {
+            // FP32 storage: the stored values' chain decides
+            static_for<0, H>([&](auto M) {
+                constexpr int m = M + 1;
+                const int rho = z >= 0 ? z / m : -((-z) / m);
+                const float v = to_f32(sm[bidx[M] + rho * C::W(m)]);
+                acc = (m == 1) ? v : acc + v;
+                if (acc > thr[M]) {
+                    hits |= 1u << M;
+                    if (write)
+                        put_record(tt.rec, rslot++, tt.cap, (uint32_t)f, z, m, 0u, acc);
+                }
+            });
+        } else {
+            // 16-bit storage.  With the FP32 copy: a level whose 16-bit sum
+            // lies within the storage error of its threshold is decided by the
+            // copy's chain (the same FP32 numbers the FP32 path forms), all of
+            // whose H values are loaded at once; without it the 16-bit sum
+            // decides and the record is flagged.
+            float pw[H];
+            uint32_t need = 0u, nearm = 0u;
+            static_for<0, H>([&](auto M) {
+                constexpr int m = M + 1;
+                const int rho = z >= 0 ? z / m : -((-z) / m);
+                const float v = to_f32(sm[bidx[M] + rho * C::W(m)]);
+                acc = (m == 1) ? v : acc + v;
+                ab += fabsf(v);
+                pw[M] = acc;
+                const float band = p.delta * ab + p.band_abs;
+                if (tt.fop32 != nullptr) {
+                    if (!(acc == acc && acc + band < thr[M]))
+                        need |= 1u << M;
+                } else {
+                    hits |= (acc > thr[M] ? 1u : 0u) << M;
+                    nearm |= (fabsf(acc - thr[M]) <= band ? 1u : 0u) << M;
+                }
+            });
+            if (need != 0u) {
+                float w[H];
+                static_for<0, H>([&](auto M) {
+                    constexpr int m = M + 1;
+                    const int rho = z >= 0 ? z / m : -((-z) / m);
+                    w[M] = __ldg(tt.fop32 + (long long)(rho + Z) * tt.ld + f / m);
+                });
+                float c = 0.f;
+                static_for<0, H>([&](auto M) {
+                    constexpr int m = M + 1;
+                    c = (m == 1) ? w[M] : c + w[M];
+                    if (((need >> M) & 1u) && c > thr[M]) {
+                        hits |= 1u << M;
+                        pw[M] = c;
+                    }
+                });
             }
-        });
+            if (write) {
+                const uint32_t fl = tt.fop32 != nullptr ? 0u : HS_FLAG_LOWP;
+                static_for<0, H>([&](auto M) {
+                    if ((hits >> M) & 1u)
+                        put_record(tt.rec, rslot++, tt.cap, (uint32_t)f, z, M + 1,
+                                   fl | (((nearm >> M) & 1u) ? HS_FLAG_NEAR : 0u), pw[M]);
+                });
+            }
+        }
         return hits;
     };
 
