@@ -327,14 +327,32 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
         return hits;
     };
 
+    // FP32: the level sums of row z (Eq. 2 order) into pw, the hit mask out
+    auto scan32 = [&](int z, float (&pw)[H]) -> uint32_t {
+        float acc = 0.f;
+        uint32_t hits = 0u;
+        float thr[H];
+        static_for<0, H>([&](auto M) { thr[M] = __ldg(p.ta + M * NT + (z + Z)); });
+        static_for<0, H>([&](auto M) {
+            constexpr int m = M + 1;
+            const int rho = z >= 0 ? z / m : -((-z) / m);
+            acc = (m == 1) ? to_f32(sm[bidx[M] + rho * C::W(m)])
+                           : acc + to_f32(sm[bidx[M] + rho * C::W(m)]);
+            pw[M] = acc;
+            hits |= (acc > thr[M] ? 1u : 0u) << M;
+        });
+        return hits;
+    };
+
     if constexpr (C::ES == 4) {
         // FP32: a dry run of the exact pass on this thread's centre row while
         // the copies are in flight (the values read are discarded): the
         // pass's code is then in the instruction cache when a marked pair
         // needs it.  (16-bit planes skip it: their pass may read the FP32
         // copy, which a dry run has no business touching.)
-        const uint32_t dry = scan(0, false, 0u);
-        asm volatile("" ::"r"(dry));
+        float pw[H];
+        const uint32_t dry = scan32(0, pw);
+        asm volatile("" ::"r"(dry), "f"(pw[H - 1]));
     }
 
     // CTA-uniform outcome of the bounded wait for the stage
@@ -485,16 +503,35 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
             mask &= mask - 1ull;
         }
         uint32_t ht = 0u, hb = 0u;
-        if (zz >= 0) {
-            ht = scan(zz, false, 0u);
-            if (zz > 0)
-                hb = scan(-zz, false, 0u);
+        if constexpr (C::ES == 4) {
+            // both rows' sums stay in registers for the write
+            float pt[H], pb[H];
+            if (zz >= 0) {
+                ht = scan32(zz, pt);
+                if (zz > 0)
+                    hb = scan32(-zz, pb);
+            }
+            uint32_t rsl = warp_reserve(tt.counters, (uint32_t)(__popc(ht) + __popc(hb)));
+            static_for<0, H>([&](auto M) {
+                if ((ht >> M) & 1u)
+                    put_record(tt.rec, rsl++, tt.cap, (uint32_t)f, zz, M + 1, 0u, pt[M]);
+            });
+            static_for<0, H>([&](auto M) {
+                if ((hb >> M) & 1u)
+                    put_record(tt.rec, rsl++, tt.cap, (uint32_t)f, -zz, M + 1, 0u, pb[M]);
+            });
+        } else {
+            if (zz >= 0) {
+                ht = scan(zz, false, 0u);
+                if (zz > 0)
+                    hb = scan(-zz, false, 0u);
+            }
+            uint32_t rsl = warp_reserve(tt.counters, (uint32_t)(__popc(ht) + __popc(hb)));
+            if (ht)
+                scan(zz, true, rsl);
+            if (hb)
+                scan(-zz, true, rsl + (uint32_t)__popc(ht));
         }
-        uint32_t rsl = warp_reserve(tt.counters, (uint32_t)(__popc(ht) + __popc(hb)));
-        if (ht)
-            scan(zz, true, rsl);
-        if (hb)
-            scan(-zz, true, rsl + (uint32_t)__popc(ht));
     }
     return true;
 }
