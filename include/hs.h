@@ -188,9 +188,11 @@ HS_API hs_status hs_run_host_checked(hs_plan *plan, const void *fop_host, void *
  * boards (Section VI-C); a pipeline has thousands per observation.  A batch
  * sums many planes of the same template count, level count and thresholds,
  * each with its own number of bins and row pitch.  Each launch carries the
- * TMA descriptors of up to K beams in its parameter block (K = 15 for the
- * 85 x 16 shape, 30 for 21 x 8) and covers the concatenated tiles of its
- * beams; a run issues ceil(n_beams / K) launches after one counter reset. */
+ * TMA descriptors of up to K beams in its parameter block (K = 13 for the
+ * 85 x 16 shape, 24 for 21 x 8) and covers the concatenated tiles of its
+ * beams; a run issues ceil(n_beams / K) launches after one counter reset.
+ * Beams packed side by side in one plane (hs_batch_set_packed) are summed
+ * by one launch whatever their number. */
 typedef struct {
     const void *fop;     /* device plane [n_templates][ld], 16-byte aligned */
     const float *fop32;  /* FP32 copy for rechecks (16-bit batches), or NULL */
@@ -219,9 +221,35 @@ HS_API hs_status hs_batch_create(hs_batch **out, int n_templates, int H, const f
 HS_API hs_status hs_batch_set_beams(hs_batch *b, const hs_beam *beams, int n_beams,
                                     hs_stream_t stream);
 
-/* Enqueue one run over every beam set by hs_batch_set_beams: one kernel
- * clears each beam's counters, then hs_batch_launches() launches sum the
- * tiles.  Records go to each beam's buffer in an unspecified order. */
+/* One beam of a packed batch: its bins are [offset, offset + n_bins) of
+ * every row of the batch's packed plane. */
+typedef struct {
+    int64_t offset;      /* first bin of the beam; offset * element size a multiple of 16 */
+    int64_t n_bins;      /* bins of this beam, >= 1; offset + n_bins <= the plane's pitch */
+    hs_cand_buf cands;   /* this beam's candidate buffer (reset by every run) */
+} hs_packed_beam;
+
+/* Describe the beams of the next runs as one packed plane: `plane` is a
+ * device array [n_templates][pitch] of the batch's dtype (16-byte aligned,
+ * pitch * element size a multiple of 16) in which the beams lie side by
+ * side along the bins (beams may share bins; bins outside every beam are
+ * never read into a result).  fop32: the FP32 copy in the same layout for
+ * 16-bit batches (NULL: records flagged HS_FLAG_LOWP), NULL for FP32.  The
+ * beam table (host array, copied) and the tile order go to device memory on
+ * `stream`.  One set of descriptors then serves every beam, so a run is one
+ * summing launch over all their tiles, whatever the beam count, after one
+ * kernel that clears every beam's counters.  The definition summed is that
+ * of hs_run (Section III, Eq. 1-2) for each beam on its own bins.  Borrowed
+ * and error rules as for hs_batch_set_beams; replaces any beam set.
+ * Errors: HS_ERR_INVALID, HS_ERR_CUDA, HS_ERR_OOM. */
+HS_API hs_status hs_batch_set_packed(hs_batch *b, const void *plane, const float *fop32,
+                                     int64_t pitch, const hs_packed_beam *beams, int n_beams,
+                                     hs_stream_t stream);
+
+/* Enqueue one run over every beam set by hs_batch_set_beams (or
+ * hs_batch_set_packed): one kernel clears each beam's counters, then
+ * hs_batch_launches() launches sum the tiles.  Records go to each beam's
+ * buffer in an unspecified order. */
 HS_API hs_status hs_batch_run(hs_batch *b, hs_stream_t stream);
 
 /* As hs_batch_run, through a CUDA graph of the same launches, captured (on
@@ -231,7 +259,7 @@ HS_API hs_status hs_batch_run(hs_batch *b, hs_stream_t stream);
 HS_API hs_status hs_batch_graph_run(hs_batch *b, hs_stream_t stream);
 
 /* Tiles of the current beam set, and the kernel launches a run issues to
- * sum them (the counter reset not included). */
+ * sum them (the counter reset not included; 1 for a packed batch). */
 HS_API int hs_batch_tiles(const hs_batch *b);
 HS_API int hs_batch_launches(const hs_batch *b);
 

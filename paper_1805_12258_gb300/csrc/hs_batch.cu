@@ -1,8 +1,11 @@
-// hs_batch.cu -- the batched form: many planes (beams) of one shape, each of
-// its own length and row pitch, summed by a few launches that each carry up
-// to K beams' TMA descriptors in their parameter block (K = 15 for the
-// 85 x 16 shape).  hs_batch_set_beams encodes the descriptors and uploads the
-// per-beam tile order; hs_batch_run launches; hs_batch_graph_run replays a
+// hs_batch.cu -- the batched form: many planes (beams) of one shape.
+// hs_batch_set_beams takes beams anywhere in device memory, each of its own
+// length and row pitch, summed by a few launches that each carry up to K
+// beams' TMA descriptors in their parameter block (K = 13 for the 85 x 16
+// shape).  hs_batch_set_packed takes beams side by side along the bins of one
+// plane: one set of descriptors serves them all and one launch sums every
+// tile of every beam, reading the beam table and the (beam, tile) run order
+// from device memory.  hs_batch_run launches; hs_batch_graph_run replays a
 // CUDA graph of the same launches, captured again after the beams change.
 #include <algorithm>
 #include <cmath>
@@ -36,6 +39,19 @@ struct hs_batch {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
     bool graph_stale = true;     // beams changed since the graph was captured
+    // packed batch (hs_batch_set_packed): one plane, one set of descriptors
+    bool packed = false;
+    CUtensorMap pmaps[kMaxStagedH];
+    CUtensorMap psplit1[2];
+    const float *pfop32 = nullptr;
+    long long pitch = 0;
+    PackedBeam *d_pbeams = nullptr;
+    int pbeams_cap = 0, n_pbeams = 0;
+    uint2 *d_ptiles = nullptr;
+    long long ptiles_cap = 0;
+    int n_ptiles = 0;
+    std::vector<uint2> h_ptiles;
+    std::vector<PackedBeam> h_pbeams;
 };
 
 namespace {
@@ -71,6 +87,35 @@ StagedBatch launch_args(const hs_batch *b)
     a.sms = b->sms;
     a.assume_nonneg = b->assume_nonneg;
     return a;
+}
+
+PackedBatch packed_args(const hs_batch *b)
+{
+    PackedBatch a{};
+    a.sh = StagedShape{b->nt, b->H, b->tb, b->dtype};
+    a.maps = b->pmaps;
+    a.split1 = b->psplit1;
+    a.tmin_host = b->tmin;
+    a.ta = b->d_ta;
+    a.fop32 = b->pfop32;
+    a.tiles = b->d_ptiles;
+    a.beams = b->d_pbeams;
+    a.n_beams = b->n_pbeams;
+    a.n_tiles = b->n_ptiles;
+    a.ld = b->pitch;
+    a.delta = b->delta;
+    a.band_abs = b->band_abs;
+    a.grid_per_sm = b->grid_per_sm;
+    a.sms = b->sms;
+    a.assume_nonneg = b->assume_nonneg;
+    return a;
+}
+
+// The launches of one run of the current beam set (on stream s).
+cudaError_t launch_run(const hs_batch *b, cudaStream_t s)
+{
+    return b->packed ? launch_packed_batch(packed_args(b), s)
+                     : launch_staged_batch(launch_args(b), s);
 }
 
 } // namespace
@@ -193,6 +238,7 @@ hs_status hs::batch_set_prepared(hs_batch *b, const StagedBatchBeam *beams, int 
     }
     b->beams.swap(nb);
     b->total_tiles = (int)total;
+    b->packed = false;
     b->graph_stale = true;
     return HS_OK;
 }
@@ -240,12 +286,128 @@ hs_status hs_batch_set_beams(hs_batch *b, const hs_beam *beams, int n_beams, hs_
     return batch_set_prepared(b, nb.data(), n_beams, reinterpret_cast<cudaStream_t>(stream));
 }
 
+hs_status hs_batch_set_packed(hs_batch *b, const void *plane, const float *fop32, int64_t pitch,
+                              const hs_packed_beam *beams, int n_beams, hs_stream_t stream)
+{
+    if (!b || (!beams && n_beams > 0))
+        return fail(HS_ERR_INVALID, "batch or beams is null");
+    if (n_beams < 0 || n_beams > b->max_beams)
+        return fail(HS_ERR_INVALID, "n_beams must be in [0, max_beams]");
+    const long long es = (long long)elem_size(b->dtype);
+    if (!plane || reinterpret_cast<uintptr_t>(plane) % 16 != 0 || pitch < 1 ||
+        pitch > 0x7fffffffLL || (pitch * es) % 16 != 0)
+        return fail(HS_ERR_INVALID, "packed plane must be 16-byte aligned with a pitch in "
+                                    "[1, 2^31) that is a multiple of 16 bytes");
+    if (fop32 && (b->dtype == HS_F32 || reinterpret_cast<uintptr_t>(fop32) % 16 != 0))
+        return fail(HS_ERR_INVALID, "bad FP32 copy (16-bit batches only; 16-byte aligned)");
+    const StagedShape sh{b->nt, b->H, b->tb, b->dtype};
+    std::vector<PackedBeam> pb((size_t)n_beams);
+    long long total = 0;
+    int most = 0;
+    for (int i = 0; i < n_beams; ++i) {
+        const hs_packed_beam &bm = beams[i];
+        if (bm.offset < 0 || bm.n_bins < 1 || bm.offset + bm.n_bins > pitch ||
+            (bm.offset * es) % 16 != 0)
+            return fail(HS_ERR_INVALID, "packed beam " + std::to_string(i) +
+                                            ": need offset >= 0 a multiple of 16 bytes, "
+                                            "n_bins >= 1, offset + n_bins <= pitch");
+        if (!bm.cands.count || (bm.cands.capacity > 0 && !bm.cands.records) ||
+            reinterpret_cast<uintptr_t>(bm.cands.records) % 16 != 0)
+            return fail(HS_ERR_INVALID, "packed beam " + std::to_string(i) +
+                                            ": bad candidate buffer");
+        PackedBeam &d = pb[(size_t)i];
+        std::memset(&d, 0, sizeof d);
+        d.off = bm.offset;
+        d.n = bm.n_bins;
+        d.rec = bm.cands.records;
+        d.counters = bm.cands.count;
+        d.cap = bm.cands.capacity;
+        const long long tiles = (bm.n_bins + b->tb - 1) / b->tb;
+        total += tiles;
+        most = std::max(most, (int)tiles);
+        if (total > 0x7fffffffLL)
+            return fail(HS_ERR_INVALID, "batch has more than 2^31 tiles");
+    }
+    CUtensorMap maps[kMaxStagedH], split1[2];
+    if (encode_plane_maps(sh, plane, pitch, pitch, maps, split1) != CUDA_SUCCESS)
+        return fail(HS_ERR_CUDA, "cuTensorMapEncodeTiled failed for the packed plane");
+    // run order: each beam's tiles in the batch's tile order, beam after beam
+    std::lock_guard<std::mutex> lk(b->mu);
+    std::vector<uint2> tiles((size_t)total);
+    {
+        const std::vector<uint32_t> full =
+            b->order == 1 ? std::vector<uint32_t>() : tile_order(most, b->order);
+        size_t at = 0;
+        for (int i = 0; i < n_beams; ++i) {
+            const int t_b = (int)((pb[(size_t)i].n + b->tb - 1) / b->tb);
+            if (b->order == 1) {
+                for (int t = 0; t < t_b; ++t)
+                    tiles[at++] = make_uint2((unsigned)i, (unsigned)t);
+            } else {
+                // the order of fewer tiles is the longer order with the
+                // larger entries dropped (its sort key depends on t alone)
+                for (uint32_t t : full)
+                    if ((int)t < t_b)
+                        tiles[at++] = make_uint2((unsigned)i, t);
+            }
+        }
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (n_beams > b->pbeams_cap || total > b->ptiles_cap) {
+        // the old tables may still be read by queued runs: wait for them
+        e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess && n_beams > b->pbeams_cap) {
+            cudaFree(b->d_pbeams);
+            b->d_pbeams = nullptr;
+            b->pbeams_cap = 0;
+            e = cudaMalloc(&b->d_pbeams, sizeof(PackedBeam) * (size_t)n_beams);
+            if (e == cudaSuccess)
+                b->pbeams_cap = n_beams;
+        }
+        if (e == cudaSuccess && total > b->ptiles_cap) {
+            cudaFree(b->d_ptiles);
+            b->d_ptiles = nullptr;
+            b->ptiles_cap = 0;
+            e = cudaMalloc(&b->d_ptiles, sizeof(uint2) * (size_t)total);
+            if (e == cudaSuccess)
+                b->ptiles_cap = total;
+        }
+        if (e != cudaSuccess)
+            return cuda_fail(e, "allocating the packed batch tables");
+    }
+    // copies from host memory this call owns until they have been read: the
+    // vectors move into the batch, which keeps them until the next set
+    b->h_pbeams.swap(pb);
+    b->h_ptiles.swap(tiles);
+    if (n_beams > 0)
+        e = cudaMemcpyAsync(b->d_pbeams, b->h_pbeams.data(), sizeof(PackedBeam) * (size_t)n_beams,
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && total > 0)
+        e = cudaMemcpyAsync(b->d_ptiles, b->h_ptiles.data(), sizeof(uint2) * (size_t)total,
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s); // the host tables may change at the next set
+    if (e != cudaSuccess)
+        return cuda_fail(e, "uploading the packed batch tables");
+    std::memcpy(b->pmaps, maps, sizeof maps);
+    std::memcpy(b->psplit1, split1, sizeof split1);
+    b->pfop32 = fop32;
+    b->pitch = pitch;
+    b->n_pbeams = n_beams;
+    b->n_ptiles = (int)total;
+    b->total_tiles = (int)total;
+    b->packed = true;
+    b->graph_stale = true;
+    return HS_OK;
+}
+
 hs_status hs_batch_run(hs_batch *b, hs_stream_t stream)
 {
     if (!b)
         return fail(HS_ERR_INVALID, "batch is null");
     std::lock_guard<std::mutex> lk(b->mu);
-    cudaError_t e = launch_staged_batch(launch_args(b), reinterpret_cast<cudaStream_t>(stream));
+    cudaError_t e = launch_run(b, reinterpret_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? HS_OK : cuda_fail(e, "batched kernel launch");
 }
 
@@ -261,7 +423,7 @@ hs_status hs_batch_graph_run(hs_batch *b, hs_stream_t stream)
         cudaGraph_t graph = nullptr;
         e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            const cudaError_t el = launch_staged_batch(launch_args(b), b->cap_stream);
+            const cudaError_t el = launch_run(b, b->cap_stream);
             e = cudaStreamEndCapture(b->cap_stream, &graph);
             if (e == cudaSuccess)
                 e = el;
@@ -294,6 +456,8 @@ int hs_batch_launches(const hs_batch *b)
 {
     if (!b)
         return 0;
+    if (b->packed)
+        return b->n_ptiles > 0 ? 1 : 0;
     const int k = staged_batch_beams_per_launch(StagedShape{b->nt, b->H, b->tb, b->dtype});
     const int n = (int)b->beams.size();
     return k > 0 ? (n + k - 1) / k : 0;
@@ -310,6 +474,8 @@ hs_status hs_batch_destroy(hs_batch *b)
         cudaStreamDestroy(b->cap_stream);
     cudaFree(b->d_ta);
     cudaFree(b->d_order);
+    cudaFree(b->d_pbeams);
+    cudaFree(b->d_ptiles);
     delete b;
     return HS_OK;
 }

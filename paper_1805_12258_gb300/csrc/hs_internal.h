@@ -110,6 +110,39 @@ struct StagedBatch {
 };
 
 bool staged_batch_available(const StagedShape &sh);
+
+// Packed batch: the beams lie side by side along the bins of one plane
+// [sh.nt][ld]; one set of descriptors (encode_plane_maps of the whole plane)
+// and one launch (after a kernel that clears every beam's counters) cover
+// them all.  Per-beam records live in device memory.
+struct PackedBeam {
+    long long off;       // first bin of the beam in the packed plane (16-byte multiple)
+    long long n;         // bins of the beam
+    hs_cand *rec;
+    uint32_t *counters;  // [0] count, [1] status
+    uint32_t cap;
+    uint32_t pad;
+};
+
+struct PackedBatch {
+    StagedShape sh;
+    const CUtensorMap *maps;   // H span descriptors of the packed plane (host copies)
+    const CUtensorMap *split1; // level-1 band descriptors of the packed plane
+    const float *tmin_host;
+    const float *ta;
+    const float *fop32;        // FP32 copy of the packed plane, or null
+    const uint2 *tiles;        // device: (beam, tile) per slot, in run order
+    const PackedBeam *beams;   // device
+    int n_beams;
+    int n_tiles;
+    long long ld;
+    float delta, band_abs;
+    int grid_per_sm;           // 0: one CTA per tile
+    int sms;
+    bool assume_nonneg;
+};
+
+cudaError_t launch_packed_batch(const PackedBatch &a, cudaStream_t s);
 int staged_batch_beams_per_launch(const StagedShape &sh);
 
 } // namespace hs

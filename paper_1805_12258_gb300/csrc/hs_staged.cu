@@ -179,15 +179,17 @@ struct TileTarget {
 };
 
 // Issue the H boxes of the tile starting at bin f0 into the stage (thread 0).
+// xoff: the bin of the plane's descriptors at which this plane starts (a
+// beam of a packed batch; 0 otherwise), a multiple of 16 bytes.
 template <int NT, int H, int TB, typename T>
 __device__ __forceinline__ void issue_tile(const TileTarget &tt, int f0, uint32_t sbase,
-                                           uint32_t bar)
+                                           uint32_t bar, int xoff = 0)
 {
     using C = Cfg<NT, H, TB, T>;
     mbar_arrive_expect_tx(bar, (uint32_t)C::TX());
     static_for<1, H + 1>([&](auto M) {
         constexpr int m = M;
-        const int x = (f0 / m) & ~(C::ALIGN - 1);
+        const int x = xoff + ((f0 / m) & ~(C::ALIGN - 1));
         tma_load_2d(sbase + C::OFF(m), &tt.maps[m - 1], x, C::Z - C::R(m), bar);
     });
 }
@@ -196,20 +198,21 @@ __device__ __forceinline__ void issue_tile(const TileTarget &tt, int f0, uint32_
 // and the spans m >= 2 complete on `bar`, the two outer bands on `bar_out`.
 template <int NT, int H, int TB, typename T>
 __device__ __forceinline__ void issue_tile_banded(const TileTarget &tt, int f0, uint32_t sbase,
-                                                  uint32_t bar, uint32_t bar_out)
+                                                  uint32_t bar, uint32_t bar_out, int xoff = 0)
 {
     using C = Cfg<NT, H, TB, T>;
     constexpr int ROWB = C::W(1) * C::ES; // bytes per level-1 row in shared memory
+    const int x1 = xoff + f0;
     mbar_arrive_expect_tx(bar, (uint32_t)C::TX_CENTRE());
-    tma_load_2d(sbase + (C::Z - C::RB) * ROWB, &tt.split1[0], f0, C::Z - C::RB, bar);
+    tma_load_2d(sbase + (C::Z - C::RB) * ROWB, &tt.split1[0], x1, C::Z - C::RB, bar);
     static_for<2, H + 1>([&](auto M) {
         constexpr int m = M;
-        const int x = (f0 / m) & ~(C::ALIGN - 1);
+        const int x = xoff + ((f0 / m) & ~(C::ALIGN - 1));
         tma_load_2d(sbase + C::OFF(m), &tt.maps[m - 1], x, C::Z - C::R(m), bar);
     });
     mbar_arrive_expect_tx(bar_out, (uint32_t)(2 * C::BYTES_OUTER));
-    tma_load_2d(sbase, &tt.split1[1], f0, 0, bar_out);
-    tma_load_2d(sbase + (C::Z + C::RB + 1) * ROWB, &tt.split1[1], f0, C::Z + C::RB + 1, bar_out);
+    tma_load_2d(sbase, &tt.split1[1], x1, 0, bar_out);
+    tma_load_2d(sbase + (C::Z + C::RB + 1) * ROWB, &tt.split1[1], x1, C::Z + C::RB + 1, bar_out);
 }
 
 // Wait for the tile's stage (phase `parity` of `bar`), run the fast pass and
@@ -759,6 +762,119 @@ __global__ void __launch_bounds__(TB, (resident_ctas<NT, H, TB, T>()))
     }
 }
 
+// Packed batch: every beam lies in one plane [NT][ld], side by side along the
+// bins (beam b at bins [off_b, off_b + n_b) of every row), so one set of
+// descriptors addresses them all and one launch sums every tile of every beam.
+template <int NT, int H, typename T>
+struct PackedParams {
+    CUtensorMap maps[H];    // spans of the packed plane, one box per stretch factor
+    CUtensorMap split1[2];  // level 1 in row bands
+    float tmin[n_groups(H)];
+    const float *ta;
+    const float *fop32;     // FP32 copy of the packed plane (same layout), or null
+    const uint2 *tiles;     // per slot: (beam, tile of that beam), in run order
+    const PackedBeam *beams;
+    long long ld;           // row pitch of the packed plane (elements)
+    float delta;
+    float band_abs;
+    int n_slots;
+};
+
+template <int NT, int H, int TB, typename T, bool SIGNCHK = true, bool BANDED = false>
+__global__ void __launch_bounds__(TB, (resident_ctas<NT, H, TB, T>()))
+    packed_kernel(const __grid_constant__ PackedParams<NT, H, T> p)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar_storage[2];
+    const uint32_t sbase = smem_addr(smem);
+    const uint32_t bar = smem_addr(&bar_storage[0]);
+    const uint32_t bar_out = smem_addr(&bar_storage[1]);
+    if (threadIdx.x == 0) {
+        static_for<0, H>([&](auto M) { prefetch_tmap(&p.maps[M]); });
+        mbar_init(bar, 1);
+        if constexpr (BANDED) {
+            prefetch_tmap(&p.split1[0]);
+            prefetch_tmap(&p.split1[1]);
+            mbar_init(bar_out, 1);
+        }
+    }
+    __syncthreads();
+    uint32_t parity = 0;
+    for (int i = (int)blockIdx.x; i < p.n_slots; i += (int)gridDim.x, parity ^= 1u) {
+        const uint2 e = __ldg(p.tiles + i);
+        const PackedBeam &pb = p.beams[e.x];
+        const long long off = __ldg(&pb.off);
+        const TileTarget tt{p.maps,
+                            p.split1,
+                            p.fop32 ? p.fop32 + off : nullptr,
+                            __ldg(&pb.n),
+                            p.ld,
+                            (hs_cand *)__ldg((const unsigned long long *)&pb.rec),
+                            (uint32_t *)__ldg((const unsigned long long *)&pb.counters),
+                            __ldg(&pb.cap)};
+        const int f0 = (int)e.y * TB;
+        if (threadIdx.x == 0) {
+            if constexpr (BANDED)
+                issue_tile_banded<NT, H, TB, T>(tt, f0, sbase, bar, bar_out, (int)off);
+            else
+                issue_tile<NT, H, TB, T>(tt, f0, sbase, bar, (int)off);
+        }
+        if (!sum_tile<NT, H, TB, T, PackedParams<NT, H, T>, CtaOr, SIGNCHK, BANDED>(
+                p, tt, f0, smem, bar, parity, CtaOr{}, bar_out))
+            break;
+        __syncthreads();
+    }
+}
+
+// Zero the counter pair of every beam of a packed batch.
+__global__ void reset_packed(const PackedBeam *beams, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        beams[i].counters[0] = 0u;
+        beams[i].counters[1] = 0u;
+    }
+}
+
+template <int NT, int H, int TB, typename T, bool SIGNCHK = true, bool BANDED = false>
+cudaError_t launch_packed_one(const PackedBatch &a, cudaStream_t s)
+{
+    using C = Cfg<NT, H, TB, T>;
+    PackedParams<NT, H, T> p;
+    std::memset(&p, 0, sizeof p);
+    std::memcpy(p.maps, a.maps, sizeof(CUtensorMap) * H);
+    std::memcpy(p.split1, a.split1, sizeof(CUtensorMap) * 2);
+    for (int g = 0; g < C::G; ++g)
+        p.tmin[g] = a.tmin_host[g];
+    p.ta = a.ta;
+    p.fop32 = a.fop32;
+    p.tiles = a.tiles;
+    p.beams = a.beams;
+    p.ld = a.ld;
+    p.delta = a.delta;
+    p.band_abs = a.band_abs;
+    p.n_slots = a.n_tiles;
+    if (a.n_beams > 0) {
+        reset_packed<<<(a.n_beams + 127) / 128, 128, 0, s>>>(a.beams, a.n_beams);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess)
+            return e;
+    }
+    if (p.n_slots <= 0)
+        return cudaSuccess;
+    auto kern = packed_kernel<NT, H, TB, T, SIGNCHK, BANDED>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess)
+        return e;
+    int grid = p.n_slots;
+    if (a.grid_per_sm > 0 && a.sms * a.grid_per_sm < grid)
+        grid = a.sms * a.grid_per_sm;
+    kern<<<grid, TB, C::SMEM, s>>>(p);
+    return cudaGetLastError();
+}
+
 // Counter pairs to clear before a batched launch, in the parameter block.
 struct CounterList {
     static constexpr int K = 1024;
@@ -1046,6 +1162,24 @@ cudaError_t launch_staged_batch(const StagedBatch &a, cudaStream_t s)
 #define X(NT_, H_, TB_, T_, DT_)                                                              \
     if (sh.nt == NT_ && sh.H == H_ && sh.tb == TB_ && sh.dtype == DT_)                       \
         return launch_batch_one<NT_, H_, TB_, T_>(a, s);
+    HS_BATCH_SHAPES(X)
+#undef X
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_packed_batch(const PackedBatch &a, cudaStream_t s)
+{
+    const StagedShape &sh = a.sh;
+    if (a.assume_nonneg) {
+#define X(NT_, H_, TB_, T_, DT_)                                                              \
+        if (sh.nt == NT_ && sh.H == H_ && sh.tb == TB_ && sh.dtype == DT_)                   \
+            return launch_packed_one<NT_, H_, TB_, T_, false, sizeof(T_) == 4>(a, s);
+        HS_BATCH_SHAPES(X)
+#undef X
+    }
+#define X(NT_, H_, TB_, T_, DT_)                                                              \
+    if (sh.nt == NT_ && sh.H == H_ && sh.tb == TB_ && sh.dtype == DT_)                       \
+        return launch_packed_one<NT_, H_, TB_, T_>(a, s);
     HS_BATCH_SHAPES(X)
 #undef X
     return cudaErrorInvalidValue;

@@ -70,6 +70,10 @@ class hs_beam(ctypes.Structure):
                 ("ld", ctypes.c_int64), ("cands", hs_cand_buf)]
 
 
+class hs_packed_beam(ctypes.Structure):
+    _fields_ = [("offset", ctypes.c_int64), ("n_bins", ctypes.c_int64), ("cands", hs_cand_buf)]
+
+
 class hs_server_config(ctypes.Structure):
     _fields_ = [("n_templates", ctypes.c_int), ("H", ctypes.c_int),
                 ("thresholds", ctypes.c_void_p), ("n_slots", ctypes.c_int),
@@ -137,6 +141,8 @@ def lib():
     L.hs_pack_paper.argtypes = [P(hs_cand), i32, P(u32), P(ctypes.c_float)]
     L.hs_batch_create.argtypes = [P(vp), i32, i32, vp, P(hs_options), i32]
     L.hs_batch_set_beams.argtypes = [vp, P(hs_beam), i32, vp]
+    L.hs_batch_set_packed.argtypes = [vp, vp, vp, i64, P(hs_packed_beam), i32, vp]
+    L.hs_batch_set_packed.restype = i32
     L.hs_batch_run.argtypes = [vp, vp]
     L.hs_batch_graph_run.argtypes = [vp, vp]
     L.hs_batch_destroy.argtypes = [vp]
@@ -439,7 +445,9 @@ def _batch_check(status, what):
 class Batch:
     """An hs_batch: many planes of one shape (each with its own bin count and
     row pitch) summed by a few launches, each carrying up to K beams'
-    descriptors; graph_run replays a captured CUDA graph of those launches."""
+    descriptors (set_beams), or beams packed side by side in one plane summed
+    by one launch (set_packed); graph_run replays a captured CUDA graph of a
+    run."""
 
     def __init__(self, n_templates, H, thresholds, *, dtype="f32", grid_per_sm=0,
                  max_beams=64, order=0, assume_nonneg=False):
@@ -467,6 +475,18 @@ class Batch:
         self._keep = list(beams)
         _batch_check(lib().hs_batch_set_beams(self.handle, arr, len(beams),
                                               _stream_handle(stream)), "hs_batch_set_beams")
+
+    def set_packed(self, plane, beams, fop32=None, stream=None):
+        """plane: tensor [n_templates][pitch] holding every beam side by side
+        along the bins; beams: list of (offset, n_bins, CandBuffer).  One
+        summing launch then covers all of them."""
+        arr = (hs_packed_beam * max(1, len(beams)))()
+        for i, (off, n_bins, cb) in enumerate(beams):
+            arr[i] = hs_packed_beam(int(off), int(n_bins), cb.c)
+        self._keep = [plane, fop32] + [b[2] for b in beams]
+        _batch_check(lib().hs_batch_set_packed(self.handle, _ptr(plane), _ptr(fop32),
+                                               int(plane.shape[-1]), arr, len(beams),
+                                               _stream_handle(stream)), "hs_batch_set_packed")
 
     @property
     def tiles(self):

@@ -152,3 +152,98 @@ def test_autotuner_picks_a_measured_option(tmp_path, monkeypatch):
     best3, table3 = autotune.tune_plane(85, 1 << 16, 16, ta, reps=2, use_cache=False)
     assert any(t[0].get("stages") == 3 and t[1] < float("inf") for t in table3)
     assert best3 in [t[0] for t in table3]
+
+
+# --- packed batch: beams side by side in one plane, one summing launch ----------
+
+def _packed(nt, sizes, seed, align=4, gap=0, dtype=torch.float32):
+    """Beams laid side by side along the bins of one plane (offsets a
+    multiple of 16 bytes, optional unused gap between beams)."""
+    offs, at = [], 0
+    for n in sizes:
+        offs.append(at)
+        at = (at + n + gap + align - 1) // align * align
+    pitch = (at + align - 1) // align * align
+    planes = [synth.noise(nt, n, seed=seed + i) for i, n in enumerate(sizes)]
+    host = np.full((nt, pitch), 1e4, np.float32)  # bins outside every beam: large
+    for off, n, pl in zip(offs, sizes, planes):
+        host[:, off:off + n] = pl
+    return planes, offs, pitch, torch.from_numpy(host).cuda()
+
+
+@pytest.mark.parametrize("nt,H,nonneg,gps,order", [(85, 16, True, 0, 0), (85, 16, False, 0, 0),
+                                                   (21, 8, True, 0, 1), (85, 16, True, 3, 2)])
+def test_packed_batch_one_launch_matches_per_plane_runs(nt, H, nonneg, gps, order):
+    rng = np.random.default_rng(41 + nt)
+    ta = synth.thresholds(1e-4, H, nt)
+    sizes = [int(x) for x in rng.integers(200, 30000, size=9)] + [129, 7, 4096]
+    planes, offs, pitch, dev = _packed(nt, sizes, seed=700, gap=13)
+    bufs = [hs.CandBuffer(1 << 16) for _ in sizes]
+    with hs.Batch(nt, H, ta, max_beams=len(sizes), assume_nonneg=nonneg, grid_per_sm=gps,
+                  order=order) as batch:
+        batch.set_packed(dev, [(o, n, cb) for o, n, cb in zip(offs, sizes, bufs)])
+        assert batch.launches == 1
+        assert batch.tiles == sum((n + 127) // 128 for n in sizes)
+        for rnd in range(3):  # run, then graph replays (records reset each time)
+            batch.graph_run() if rnd else batch.run()
+            for plane, cb in zip(planes, bufs):
+                got, cnt, st = cb.fetch()
+                assert st == hs.HS_OK
+                assert np.array_equal(got, _plan_records(plane, H, ta))
+
+
+def test_packed_batch_beam_against_oracle():
+    # a ragged beam in the middle of the packed plane and the last one, which
+    # ends at the plane's edge, against the FP64 oracle
+    nt, H = 85, 16
+    ta = synth.thresholds(1e-4, H, nt)
+    sizes = [5000, 12345, 3001]
+    planes, offs, pitch, dev = _packed(nt, sizes, seed=900)
+    assert offs[-1] + sizes[-1] <= pitch
+    bufs = [hs.CandBuffer(1 << 16) for _ in sizes]
+    with hs.Batch(nt, H, ta, max_beams=4, assume_nonneg=True) as batch:
+        batch.set_packed(dev, [(o, n, cb) for o, n, cb in zip(offs, sizes, bufs)])
+        batch.run()
+    for plane, cb in zip(planes[1:], bufs[1:]):
+        got, cnt, st = cb.fetch()
+        ref, near = oracle.detect(plane, H, ta, threads=8)
+        assert st == hs.HS_OK and cnt > 0
+        near_keys = {(int(c["k"]), int(c["z"]), int(c["f"])) for c in near}
+        g = {(int(r["k"]), int(r["z"]), int(r["bin"])): float(r["power"]) for r in got}
+        o = {(int(c["k"]), int(c["z"]), int(c["f"])): float(c["power"]) for c in ref}
+        assert not ((set(g) ^ set(o)) - near_keys)
+        for k in set(g) & set(o):
+            assert abs(g[k] - o[k]) <= 1e-6 * abs(o[k])
+
+
+def test_packed_batch_bf16_with_recheck_equals_fp32_records():
+    nt, H = 85, 16
+    ta = synth.thresholds(1e-4, H, nt)
+    sizes = [7000, 2500, 9999]
+    planes, offs, pitch, dev32 = _packed(nt, sizes, seed=950, align=8)
+    dev16 = dev32.to(torch.bfloat16)
+    bufs = [hs.CandBuffer(1 << 16) for _ in sizes]
+    with hs.Batch(nt, H, ta, dtype="bf16", max_beams=4, assume_nonneg=True) as batch:
+        batch.set_packed(dev16, [(o, n, cb) for o, n, cb in zip(offs, sizes, bufs)],
+                         fop32=dev32)
+        batch.graph_run()
+    for plane, cb in zip(planes, bufs):
+        got, cnt, st = cb.fetch()
+        assert st == hs.HS_OK
+        assert np.array_equal(got, _plan_records(plane, H, ta))
+
+
+def test_packed_batch_rejects_bad_layouts():
+    nt, H = 85, 16
+    ta = synth.thresholds(1e-4, H, nt)
+    dev = torch.zeros((nt, 1024), device="cuda")
+    cb = hs.CandBuffer(16)
+    with hs.Batch(nt, H, ta, max_beams=4) as batch:
+        for beams in ([(2, 100, cb)],          # offset not a multiple of 16 bytes
+                      [(1000, 100, cb)],       # beyond the pitch
+                      [(0, 0, cb)]):           # empty beam
+            with pytest.raises(hs.HsError) as e:
+                batch.set_packed(dev, beams)
+            assert e.value.status == hs.HS_ERR_INVALID
+        with pytest.raises(hs.HsError):
+            batch.set_packed(dev[:, 1:], [(0, 100, cb)])  # misaligned plane / pitch
