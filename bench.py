@@ -204,12 +204,15 @@ def host_cores():
         return os.cpu_count() or 1
 
 
+KERNEL_SOURCES = ("hs_staged.cuh", "hs_device.cuh")
+
+
 def kernel_source_hash():
-    """Hash of the staged kernel's code (hs_staged.cu + hs_device.cuh) with
+    """Hash of the staged kernel's code (hs_staged.cuh + hs_device.cuh) with
     comments and white space removed, so comment edits keep a profile valid."""
     import re
     h = hashlib.sha256()
-    for f in ("hs_staged.cu", "hs_device.cuh"):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_1805_12258_gb300", "csrc", f)) as fh:
             code = fh.read()
         code = re.sub(r"/\*.*?\*/", "", code, flags=re.S)

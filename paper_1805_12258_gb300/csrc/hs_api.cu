@@ -119,7 +119,8 @@ CUresult hs::encode_plane_maps(const StagedShape &sh, const void *base, long lon
         encode_tensor_map(&split1[0], sh.dtype, base, n_bins, ld, sh.nt, w, 2 * rb + 1);
     if (r != CUDA_SUCCESS)
         return r;
-    return encode_tensor_map(&split1[1], sh.dtype, base, n_bins, ld, sh.nt, w, z - rb);
+    return encode_tensor_map(&split1[1], sh.dtype, base, n_bins, ld, sh.nt, w,
+                             std::max(1, z - rb));
 }
 
 void hs::storage_error(int dtype, int H, float *delta, float *band_abs)
@@ -290,6 +291,7 @@ hs_status launch_range(hs_plan *p, const void *fop, const float *fop32, cudaStre
         L.ring_zs = p->ring_zs;
         L.assume_nonneg = p->opt.assume_nonneg != 0;
         L.ring_stages = p->ring_stages;
+        L.nt_rt = p->nt;
         e = launch_staged(L, s);
         if (e != cudaSuccess)
             return cuda_fail(e, "staged kernel launch");
@@ -425,8 +427,10 @@ hs_status hs_plan_create(hs_plan **out, int n_templates, int64_t n_bins, int H,
     if (o.kernel == HS_KERNEL_STAGED && !staged_ok) {
         delete p;
         return fail(HS_ERR_UNSUPPORTED, "no staged kernel for this shape/options "
-                                        "(compiled: 85x16 and 21x8, stretch, symmetric, "
-                                        "rows a multiple of 16 bytes)");
+                                        "(compiled: 85x16 and 21x8; FP32 also any odd "
+                                        "template count up to 85 at H = 8 or 16 and up to "
+                                        "127 at H = 16; stretch, symmetric, rows a "
+                                        "multiple of 16 bytes)");
     }
     if (o.kernel == HS_KERNEL_GENERIC || !staged_ok) {
         p->kernel = HS_KERNEL_GENERIC;

@@ -74,6 +74,8 @@ struct StagedLaunch {
     int grid_per_sm;          // 0: one CTA per tile; k > 0: k resident CTAs per SM
     int ring_zs, ring_stages; // > 0: the pipelined kernel, consumer groups and stages
     bool assume_nonneg;       // the caller declares the plane non-negative
+    int nt_rt;                // the plane's template count (0: sh.nt); a kernel family with
+                              // runtime rows serves any odd count up to its compiled one
 };
 
 // True when the pipelined kernel is compiled for this shape, groups and stages.

@@ -160,6 +160,7 @@ extern "C" hs_status hs_run_noalloc(int n_templates, int64_t n_bins, int H,
         L.ld = n_bins;
         L.tile_lo = 0;
         L.tile_hi = (int)((n_bins + tb - 1) / tb);
+        L.nt_rt = n_templates;
         e = launch_staged(L, s);
     } else {
         GenericArgs a{};

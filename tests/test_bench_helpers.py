@@ -15,7 +15,7 @@ CSRC = os.path.join("paper_1805_12258_gb300", "csrc")
 
 def _copy_sources(root):
     os.makedirs(os.path.join(root, CSRC))
-    for f in ("hs_staged.cu", "hs_device.cuh"):
+    for f in bench.KERNEL_SOURCES:
         shutil.copy(os.path.join(bench.ROOT, CSRC, f), os.path.join(root, CSRC, f))
 
 
@@ -23,7 +23,7 @@ def test_hash_ignores_comments_and_spacing(tmp_path, monkeypatch):
     _copy_sources(tmp_path)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     h0 = bench.kernel_source_hash()
-    path = os.path.join(tmp_path, CSRC, "hs_staged.cu")
+    path = os.path.join(tmp_path, CSRC, bench.KERNEL_SOURCES[0])
     src = open(path).read()
     open(path, "w").write("// a new comment\n/* and a block\n comment */\n" +
                           src.replace("\n", "\n\n", 3))

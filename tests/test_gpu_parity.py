@@ -508,3 +508,32 @@ def test_ska_plane_row_sums(ska, z, assume_nonneg):
     f = np.arange(wl.n_bins, dtype=np.int64)
     ref = oracle.sample(plane, wl.H, np.full(wl.n_bins, z, np.int32), f)
     np.testing.assert_allclose(got, ref, rtol=RTOL, atol=0)
+
+
+# --- other plane shapes: kernel families with runtime rows ------------------------
+
+@pytest.mark.parametrize("nt,n,H", [(85, 2500, 8), (43, 3000, 16), (127, 1500, 16),
+                                    (83, 700, 16), (15, 1000, 8), (1, 300, 16)])
+@pytest.mark.parametrize("assume_nonneg", [False, True])
+def test_other_shapes_every_level_sum(nt, n, H, assume_nonneg):
+    # 85 x 8 (the paper's N_hp = 8 on the full template set), 43 and 83
+    # templates at 16 levels, 127 templates, one template: a staged kernel
+    # compiled for more rows serves the plane (boxes centred on its centre
+    # row, rows outside it filled with zeros and never read)
+    plane = synth.noise(nt, n, seed=nt * 7 + n)
+    got, used = _all_sums(plane, H, assume_nonneg=assume_nonneg)
+    assert used == "staged"
+    ref = oracle.planes(plane, H)
+    np.testing.assert_allclose(got, ref, rtol=RTOL, atol=0)
+
+
+@pytest.mark.parametrize("nt,n,H", [(85, 40000, 8), (43, 30000, 16), (127, 20000, 16)])
+@pytest.mark.parametrize("assume_nonneg", [False, True])
+def test_other_shapes_candidates(nt, n, H, assume_nonneg):
+    wl = synth.Workload("shape", nt, n, H, 11, 1e-6, 8, (500, 2000), (-1, 1))
+    plane = synth.make_plane(wl)
+    ta = synth.thresholds(1e-5, H, nt)
+    recs, cnt, st, used = run_gpu(plane, H, ta, assume_nonneg=assume_nonneg)
+    assert used == "staged" and st == hs.HS_OK and cnt == len(recs) > 0
+    ref, near = oracle.detect(plane, H, ta, threads=8)
+    assert_matches_oracle(recs, ref, near)
