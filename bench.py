@@ -17,6 +17,16 @@ roofline   : the staged kernel's algorithmic bytes per launch (plane once +
 cpu_baseline: the FP64 oracle on a bounded sample of the same plane, all host
              cores (threads over bin ranges).
 --impl reference: the oracle alone, timed on the host cores (rank 0 only).
+
+The default line also carries, each measured on its own after the main
+measurement (skipped with --no-extras, and for every other workload):
+precision  the same plane stored as BF16 and as FP16 (FP32 recheck copy):
+           kernel time, throughput, roofline on its own bytes, records equal
+           to the FP32 path's;
+batch      64 beams log-uniform in [2^18, 2^22] bins packed in one plane, one
+           summing launch per graph replay, against back-to-back hs_runs;
+serve      the serving engine for 2 s of Poisson arrivals at 1000 beams/s:
+           p50/p99 latency, then closed-loop capacity.
 """
 from __future__ import annotations
 
@@ -78,6 +88,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU work of the oracle sample (core-seconds)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload: skip the precision, batch and serve sections "
+                         "added to the line after the main measurement")
     return ap.parse_args()
 
 
@@ -294,6 +307,55 @@ def run_reference(args):
     }), flush=True)
 
 
+# ---- sections of the default line: the other forms ------------------------------------
+
+def precision_summary(fop32, ta, H, ref_records, nonneg, steps=500):
+    """The plane stored as BF16 and as FP16 (rounded on the device), summed
+    with FP32 accumulation, levels near a threshold re-decided from the FP32
+    copy; per storage: mean kernel time (plan events), throughput, roofline
+    on its own bytes, and whether its records equal the FP32 path's."""
+    import torch
+
+    from paper_1805_12258_gb300 import hs
+    nt, n = fop32.shape
+    stream = torch.cuda.current_stream()
+    peak, kind = peaks()
+    out = {}
+    for dt, tdt in (("bf16", torch.bfloat16), ("f16", torch.float16)):
+        low = fop32.to(tdt)
+        c = hs.CandBuffer(1 << 20)
+        with hs.Plan(nt, n, H, ta, dtype=dt, assume_nonneg=nonneg) as plan:
+            for _ in range(10):
+                plan.run(low, c, stream, fop_f32=fop32)
+            torch.cuda.synchronize()
+            clocks = ClockSampler(torch.cuda.current_device())
+            clocks.start()
+            time.sleep(0.3)
+            plan.set_timing(True)
+            plan.kernel_time()
+            for _ in range(steps):
+                plan.run(low, c, stream, fop_f32=fop32)
+            torch.cuda.synchronize()
+            clk = clocks.stop()
+            ms, k = plan.kernel_time()
+            plan.set_timing(False)
+            recs, cnt, st = c.fetch(stream)
+        us = ms / max(k, 1) * 1e3
+        algo = nt * n * 2 + H * nt * 4 + 16 * int(cnt) + 8
+        out[dt] = {"storage": dt, "recheck": "FP32 copy", "mean_kernel_us": us,
+                   "points_per_s": nt * n / (us / 1e6), "candidates": int(cnt),
+                   "records_equal_fp32_path": bool(np.array_equal(recs, ref_records)),
+                   "status": hs.hs_status_str(st),
+                   "roofline": {"bound": "hbm", "achieved": algo / (us / 1e6) / 1e9,
+                                "peak": peak, "unit": "GB/s",
+                                "frac": algo / (us / 1e6) / 1e9 / peak,
+                                "peak_kind": f"{kind} copy bandwidth",
+                                "algo_bytes_per_launch": algo},
+                   "clocks": clk}
+        del low
+    return out
+
+
 # ---- our arm ------------------------------------------------------------------------
 
 def run_ours(args):
@@ -467,6 +529,18 @@ def run_ours(args):
             parity = window_parity(timed_records, cpu)
         cpu = {k: v for k, v in cpu.items() if not k.startswith("_")}
 
+    sections = {}
+    if (rank == 0 and ws == 1 and not args.no_extras and args.workload == "ska" and
+            args.dtype == "f32" and args.index == "stretch" and not band):
+        # the other forms of the method, each measured on its own after the
+        # main measurement: 16-bit storage of this plane, the 64-beam batch,
+        # a short serving run
+        sections["precision"] = precision_summary(fop, ta, H, timed_records,
+                                                  not args.check_signs)
+        sections["batch"] = batch_summary(args, steps=20, tune=False)
+        torch.cuda.empty_cache()
+        sections["serve"] = serve_summary(args, seconds=2.0, rate=1000.0, closed_k=1000)
+        torch.cuda.empty_cache()
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -499,7 +573,9 @@ def run_ours(args):
                          "kernel": kname, "algo_bytes_per_launch": algo_bytes,
                          "mean_kernel_us": mean_kernel_s * 1e6,
                          "frac_of_8tbs": algo_bytes / mean_kernel_s / 8e12},
-            "precision": precision,
+            "precision": precision if precision is not None else sections.get("precision"),
+            "batch": sections.get("batch"),
+            "serve": sections.get("serve"),
             "parity_in_window": None if parity is None else parity["equal"],
             "parity_window": parity,
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
@@ -511,49 +587,58 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_batch(args):
-    """64 beams of 85 templates x n_bins (log-uniform in [2^18, 2^22]),
-    H = 16, FP32, summed by one graph replay (counter reset + batched
-    launches) per step; the same beams through one hs_run each, back to back
-    on the stream, are timed beside it."""
+def packed_beams(nt, sizes, seed):
+    """Beams of the given lengths side by side along the bins of one device
+    plane (offsets a multiple of 4 bins = 16 bytes), Exponential(1) noise
+    drawn on the device; returns (plane, offsets)."""
+    import torch
+    offs, at = [], 0
+    for n in sizes:
+        offs.append(at)
+        at = (at + n + 3) // 4 * 4
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    plane = torch.empty((nt, at), device="cuda").exponential_(generator=g)
+    return plane, offs
+
+
+def batch_summary(args, *, n_beams=64, lo=18.0, hi=22.0, steps=20, tune=False):
+    """64 beams of 85 templates x n_bins (log-uniform in [2^lo, 2^hi], seed
+    3), H = 16, FP32, packed side by side in one plane and summed by one
+    graph replay per step (a counter reset and one summing launch); the same
+    beams as one hs_run each, back to back, are timed beside it and their
+    records compared.  tune: the autotuner picks the launch form (packed, or
+    launches carrying each beam's descriptors), tile order and grid."""
     import torch
 
-    from paper_1805_12258_gb300 import autotune
-    from paper_1805_12258_gb300 import build as hsbuild
-    from paper_1805_12258_gb300 import hs, synth
-
-    torch.cuda.set_device(0)
-    hsbuild.build()
+    from paper_1805_12258_gb300 import autotune, hs, synth
     nt, H = 85, 16
-    lo, hi = (float(x) for x in args.beam_log2.split(","))
-    sizes = [int(x) for x in synth.beam_lengths(args.beams, seed=3, lo_log2=lo, hi_log2=hi)]
+    sizes = [int(x) for x in synth.beam_lengths(n_beams, seed=3, lo_log2=lo, hi_log2=hi)]
     ta = synth.thresholds(1e-8, H, nt)
-    beams, planes = [], []
-    for i, n in enumerate(sizes):
-        ld = (n + 3) // 4 * 4
-        g = torch.Generator(device="cuda")
-        g.manual_seed(3000 + i)
-        dev = torch.empty((nt, ld), device="cuda").exponential_(generator=g)
-        beams.append((dev, n, hs.CandBuffer(1 << 16)))
+    plane, offs = packed_beams(nt, sizes, seed=3000)
+    pitch = plane.shape[1]
+    bufs = [hs.CandBuffer(1 << 16) for _ in sizes]
+    beams = [(plane[:, o:], n, cb) for o, n, cb in zip(offs, sizes, bufs)]
+    nonneg = not args.check_signs
+    choice, table = {"form": "packed", "order": 0, "grid_per_sm": 0}, None
+    if tune:
+        choice, table = autotune.tune_batch(nt, H, ta, beams, assume_nonneg=nonneg,
+                                            packed=(plane, offs))
     points = nt * sum(sizes)
-    gps, order = args.grid_per_sm, args.order
-    tuned = None
-    if gps is None or gps < 0:  # the autotuner chooses tile order and grid
-        best, table = autotune.tune_batch(nt, H, ta, beams, assume_nonneg=not args.check_signs)
-        gps, order = best["grid_per_sm"], best.get("order", args.order)
-        tuned = table
     stream = torch.cuda.current_stream()
-    with hs.Batch(nt, H, ta, grid_per_sm=gps, max_beams=len(beams), order=order,
-                  assume_nonneg=not args.check_signs) as batch:
-        batch.set_beams(beams)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with hs.Batch(nt, H, ta, grid_per_sm=choice["grid_per_sm"], max_beams=len(sizes),
+                  order=choice["order"], assume_nonneg=nonneg) as batch:
+        if choice["form"] == "packed":
+            batch.set_packed(plane, [(o, n, cb) for o, n, cb in zip(offs, sizes, bufs)])
+        else:
+            batch.set_beams(beams)
         for _ in range(max(3, args.warmup)):
             batch.graph_run(stream)
         torch.cuda.synchronize()
-        steps = max(3, min(args.steps, 200))
         clocks = ClockSampler(0)
         clocks.start()
         time.sleep(0.3)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(steps):
             batch.graph_run(stream)
@@ -561,74 +646,92 @@ def run_batch(args):
         torch.cuda.synchronize()
         clk = clocks.stop()
         ms = e0.elapsed_time(e1) / steps
-        n_cand = sum(b[2].sync()[1] for b in beams)
-        tiles = batch.tiles
-        launches = batch.launches
+        rec_batch = [cb.fetch(stream)[0] for cb in bufs]
+        tiles, launches = batch.tiles, batch.launches
     # the same beams one hs_run each, back to back on the stream
-    plans = [hs.Plan(nt, n, H, ta, row_pitch=dev.shape[1], assume_nonneg=not args.check_signs)
-             for dev, n, _ in beams]
+    seq_bufs = [hs.CandBuffer(1 << 16) for _ in sizes]
+    plans = [hs.Plan(nt, n, H, ta, row_pitch=pitch, assume_nonneg=nonneg) for n in sizes]
     try:
         def sequential():
-            for plan, (dev, n, cb) in zip(plans, beams):
-                plan.run(dev, cb, stream=stream)
+            for plan, o, cb in zip(plans, offs, seq_bufs):
+                plan.run(plane[:, o:], cb, stream=stream)
         for _ in range(3):
             sequential()
         torch.cuda.synchronize()
-        seq_steps = max(3, min(steps, 20))
+        seq_steps = max(3, min(steps, 10))
         e0.record(stream)
         for _ in range(seq_steps):
             sequential()
         e1.record(stream)
         torch.cuda.synchronize()
         t_seq = e0.elapsed_time(e1) / seq_steps
+        rec_seq = [cb.fetch(stream)[0] for cb in seq_bufs]
     finally:
         for plan in plans:
             plan.close()
-    algo = nt * sum(sizes) * 4 + H * nt * 4 + 16 * n_cand + 8 * len(beams)
+    n_cand = int(sum(len(r) for r in rec_batch))
+    algo = nt * sum(sizes) * 4 + H * nt * 4 + 16 * n_cand + 8 * len(sizes)
     peak, kind = peaks()
-    print(json.dumps({
-        "metric": METRIC, "value": points / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
-        "steps": steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic (planes generated on the device)",
-        "config": {"workload": f"batch of {len(beams)} beams, 85 templates x n_bins "
-                               f"log-uniform in [2^{lo:g}, 2^{hi:g}], H=16 fp32",
-                   "beams": len(beams), "bins_total": sum(sizes), "tiles": tiles,
-                   "launches_per_step": 1 + launches,
-                   "inputs": "checked for negative values" if args.check_signs else
-                             "declared non-negative (powers)",
-                   "tile_order": ORDER_NAMES.get(order, str(order)),
-                   "grid_per_sm": gps, "graph": True, "candidates": n_cand,
-                   "l2": "inputs larger than L2, no flush"},
-        "sequential_hs_run_ms": t_seq, "batch_speedup_vs_sequential": t_seq / ms,
-        "sequential": "one hs_run per beam back to back on the stream, CUDA events around "
-                      "the whole sequence",
+    del plane, beams
+    return {
+        "workload": f"batch of {len(sizes)} beams, 85 templates x n_bins log-uniform in "
+                    f"[2^{lo:g}, 2^{hi:g}], H=16 fp32",
+        "beams": len(sizes), "bins_total": sum(sizes), "tiles": tiles,
+        "form": choice["form"], "tile_order": ORDER_NAMES.get(choice["order"], choice["order"]),
+        "grid_per_sm": choice["grid_per_sm"],
+        "launches_per_step": 1 + launches, "graph": True, "ms_per_step": ms,
+        "points_per_s": points / (ms / 1e3), "candidates": n_cand,
+        "sequential_hs_run_ms": t_seq, "speedup_vs_sequential": t_seq / ms,
+        "records_equal_per_plane_runs": all(np.array_equal(a, b)
+                                            for a, b in zip(rec_batch, rec_seq)),
+        "inputs": "checked for negative values" if args.check_signs else
+                  "declared non-negative (powers)",
         "roofline": {"bound": "hbm", "achieved": algo / (ms / 1e3) / 1e9, "peak": peak,
-                     "unit": "GB/s", "frac": algo / (ms / 1e3) / 1e9 / peak, "traffic": None,
-                     "peak_kind": f"{kind} copy bandwidth", "kernel": "batched 85x16 f32",
-                     "algo_bytes_per_launch": algo,
-                     "timed": "CUDA events around the graph replays (counter reset + "
-                              "batched launches)"},
-        "autotune": tuned, "e2e": None, "cpu_baseline": None, "clocks": clk,
-        "gpu_launches": (1 + launches) * steps,
+                     "unit": "GB/s", "frac": algo / (ms / 1e3) / 1e9 / peak,
+                     "peak_kind": f"{kind} copy bandwidth", "algo_bytes_per_step": algo,
+                     "frac_of_8tbs": algo / (ms / 1e3) / 8e12},
+        "timed": "CUDA events around the graph replays (counter reset + summing launches)",
+        "autotune": table, "clocks": clk,
+    }
+
+
+def run_batch(args):
+    """The batch workload as its own line (see batch_summary)."""
+    import torch
+
+    from paper_1805_12258_gb300 import build as hsbuild
+    torch.cuda.set_device(0)
+    hsbuild.build()
+    lo, hi = (float(x) for x in args.beam_log2.split(","))
+    tune = args.grid_per_sm is None or args.grid_per_sm < 0
+    steps = max(3, min(args.steps, 200))
+    b = batch_summary(args, n_beams=args.beams, lo=lo, hi=hi, steps=steps, tune=tune)
+    print(json.dumps({
+        "metric": METRIC, "value": b["points_per_s"], "unit": UNIT, "n_gpus": 1,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": b["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (planes generated on the device)",
+        "config": {k: v for k, v in b.items() if k not in ("roofline", "clocks", "autotune")},
+        "roofline": b["roofline"], "autotune": b["autotune"], "e2e": None,
+        "cpu_baseline": None, "clocks": b["clocks"],
+        "gpu_launches": b["launches_per_step"] * steps,
     }), flush=True)
 
 
-def run_serve(args):
-    """The serving engine under Poisson arrivals (seed 4) of beams with
-    85 templates x n_bins log-uniform in [2^18, 2^22], H = 16, FP32 or BF16
-    (50/50), 0-10 injected signals each; then a closed-loop phase that keeps
-    the queue full to measure the engine's capacity."""
+def serve_summary(args, seconds, rate, closed_k=None):
+    """The serving engine under Poisson arrivals (seed 4, `rate` beams/s for
+    `seconds`) of beams with 85 templates x n_bins log-uniform in
+    [2^18, 2^22], H = 16, FP32 or BF16 (50/50), 0-10 injected signals each;
+    then closed-loop phases that keep the queue full to measure the engine's
+    capacity, with planes generated per request and with planes already
+    resident.  Returns a summary dict."""
     import threading
 
     import numpy as np
     import torch
 
-    from paper_1805_12258_gb300 import build as hsbuild
     from paper_1805_12258_gb300 import hs, synth
 
-    torch.cuda.set_device(0)
-    hsbuild.build()
     nt, H = 85, 16
     ta = synth.thresholds(1e-8, H, nt)
     rng = np.random.Generator(np.random.Philox(4))
@@ -689,16 +792,16 @@ def run_serve(args):
             return results, rejected[0]
 
         # open loop: Poisson arrivals
-        k = int(args.serve_rate * args.serve_seconds * 1.2) + 16
-        gaps = rng.exponential(1.0 / args.serve_rate, size=k)
+        k = int(rate * seconds * 1.2) + 16
+        gaps = rng.exponential(1.0 / rate, size=k)
         arr = np.cumsum(gaps)
-        k = int(np.searchsorted(arr, args.serve_seconds))
+        k = int(np.searchsorted(arr, seconds))
         n_bins, dts, sigs = draw(k)
         clocks = ClockSampler(0)
         clocks.start()
         res_open, rej = phase(n_bins, dts, sigs, arr[:k], 2 * 10**6)
         # closed loop: queue kept full for capacity
-        kc = max(64, int(args.serve_rate * 3))
+        kc = closed_k or max(64, int(rate * 3))
         cn, cd, cs = draw(kc)
         res_closed, _ = phase(cn, cd, cs, None, 3 * 10**6)
         # closed loop over planes already resident (made upstream beforehand):
@@ -717,7 +820,7 @@ def run_serve(args):
                 hs.hs_synth_fop(b16, f32, "bf16", nt, n, ld, 5 * 10**6 + i, 5)
                 pool.append((n, "bf16", b16, f32))
         torch.cuda.synchronize()
-        kr = max(64, int(args.serve_rate * 3))
+        kr = closed_k or max(64, int(rate * 3))
         res_res, rtickets = [], []
         done_r = threading.Event()
 
@@ -782,25 +885,41 @@ def run_serve(args):
             torch.cuda.synchronize()
         gen[name] = e0.elapsed_time(e1)
     del f32, b16
-    print(json.dumps({
-        "metric": "FOP points harmonic-summed/s served (planes resident, queue kept full)",
-        "value": sr["points_per_s"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16",
-        "data": "synthetic (planes generated on the device per request)",
-        "config": {"workload": f"serving: Poisson {args.serve_rate:g} beams/s for "
-                               f"{args.serve_seconds:g} s, 85 templates x n_bins log-uniform in "
-                               f"[2^{lo:g}, 2^{hi:g}], H=16, FP32/BF16 50/50, 0-10 signals",
-                   "slots": args.slots, "l2": "inputs larger than L2",
-                   "inputs": "checked for negative values" if args.check_signs else
-                             "declared non-negative (powers)"},
-        "open_loop": dict(so, rejected=rej, offered_per_s=args.serve_rate),
+    return {
+        "workload": f"serving: Poisson {rate:g} beams/s for {seconds:g} s, 85 templates x "
+                    f"n_bins log-uniform in [2^{lo:g}, 2^{hi:g}], H=16, FP32/BF16 50/50, "
+                    "0-10 signals",
+        "slots": args.slots,
+        "inputs": "checked for negative values" if args.check_signs else
+                  "declared non-negative (powers)",
+        "open_loop": dict(so, rejected=rej, offered_per_s=rate),
         "closed_loop": sc,
         "closed_loop_resident_planes": dict(sr, note="planes made beforehand and kept "
                                             "resident; requests sum them in place"),
         "latency": "steady clock from hs_server_submit to the candidates in host memory "
                    "(service: from admission into a slot)",
-        "generator_ms_per_2^22_plane": gen,
-        "stats": st, "clocks": clk, "e2e": None, "cpu_baseline": None,
+        "generator_ms_per_2^22_plane": gen, "stats": st, "clocks": clk,
+    }
+
+
+def run_serve(args):
+    """The serving workload as its own line (see serve_summary)."""
+    import torch
+
+    from paper_1805_12258_gb300 import build as hsbuild
+    torch.cuda.set_device(0)
+    hsbuild.build()
+    sv = serve_summary(args, args.serve_seconds, args.serve_rate)
+    print(json.dumps({
+        "metric": "FOP points harmonic-summed/s served (planes resident, queue kept full)",
+        "value": sv["closed_loop_resident_planes"]["points_per_s"], "unit": UNIT, "n_gpus": 1,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16",
+        "data": "synthetic (planes generated on the device per request)",
+        "config": {"workload": sv["workload"], "slots": sv["slots"],
+                   "l2": "inputs larger than L2", "inputs": sv["inputs"]},
+        **{k: sv[k] for k in ("open_loop", "closed_loop", "closed_loop_resident_planes",
+                              "latency", "generator_ms_per_2^22_plane", "stats", "clocks")},
+        "e2e": None, "cpu_baseline": None,
     }), flush=True)
 
 

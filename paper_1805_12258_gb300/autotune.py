@@ -1,7 +1,8 @@
 """Autotuner for the staged kernel: tile width, tile order and launch form
 (one CTA per tile, k resident CTAs per SM walking tiles, or the pipelined
-ring with its staging depth and consumer groups) for a plane shape; tile
-order and resident CTAs per SM for batches.
+ring with its staging depth and consumer groups) for a plane shape; for
+batches the launch form (one launch over a packed plane, or launches that
+carry each beam's descriptors), tile order and resident CTAs per SM.
 
 Each candidate is timed on the GPU with the plan's kernel events (device time
 of the kernel launches only); the best choice is cached in a JSON file keyed
@@ -26,7 +27,7 @@ _lock = threading.Lock()
 LAUNCH_FORMS = ({"grid_per_sm": 0}, {"grid_per_sm": 3}, {"stages": 3, "z_split": 2},
                 {"stages": 3, "z_split": 3})
 PLANE_SPACE = {"tile_bins": (64, 96, 128), "order": (1, 2, 3), "launch": LAUNCH_FORMS}
-BATCH_SPACE = {"order": (2, 3), "grid_per_sm": (0, 3, 6)}
+BATCH_SPACE = {"form": ("packed", "beams"), "order": (2, 3), "grid_per_sm": (0, 3)}
 
 
 def cache_path() -> str:
@@ -109,29 +110,39 @@ def tune_plane(n_templates, n_bins, H, thresholds, *, dtype="f32", fop=None, rep
 
 
 def tune_batch(n_templates, H, thresholds, beams, *, dtype="f32", reps=5, use_cache=True,
-               space=None, assume_nonneg=False):
-    """Best resident CTAs per SM for a batch of beams [(fop, n_bins, CandBuffer), ...]."""
+               space=None, assume_nonneg=False, packed=None):
+    """Best launch form, tile order and resident CTAs per SM for a batch of
+    beams [(fop, n_bins, CandBuffer), ...].  packed: (plane, offsets) holding
+    the same beams side by side in one plane, to time the single-launch
+    form too (skipped when None)."""
     import torch
     n_rep = int(np.median([b[1] for b in beams]))
     key = key_of(f"batch{len(beams)}{'+' if assume_nonneg else ''}", n_templates, H, dtype,
                  n_rep)
     if use_cache and key in _load():
         return _load()[key]["best"], _load()[key]["table"]
-    space = space or BATCH_SPACE
+    space = dict(space or BATCH_SPACE)
+    forms = [f for f in space.get("form", ("beams",)) if f == "beams" or packed is not None]
     table = []
-    for order, gps in itertools.product(space.get("order", (0,)), space["grid_per_sm"]):
+    for form, order, gps in itertools.product(forms, space.get("order", (0,)),
+                                              space["grid_per_sm"]):
         with hs.Batch(n_templates, H, thresholds, dtype=dtype, grid_per_sm=gps, order=order,
                       max_beams=len(beams), assume_nonneg=assume_nonneg) as b:
-            b.set_beams(beams)
-            b.run()
+            if form == "packed":
+                plane, offs = packed
+                b.set_packed(plane, [(o, n, cb) for o, (_, n, cb) in zip(offs, beams)])
+            else:
+                b.set_beams(beams)
+            b.graph_run()
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             for _ in range(reps):
-                b.run()
+                b.graph_run()
             e1.record()
             torch.cuda.synchronize()
-            table.append(({"order": order, "grid_per_sm": gps}, e0.elapsed_time(e1) / reps))
+            table.append(({"form": form, "order": order, "grid_per_sm": gps},
+                          e0.elapsed_time(e1) / reps))
     best = min(table, key=lambda x: x[1])[0]
     _store(key, {"best": best, "table": table})
     return best, table

@@ -464,13 +464,14 @@ class Batch:
         self._keep = []
 
     def set_beams(self, beams, stream=None):
-        """beams: list of (fop tensor [n_templates][ld], n_bins, CandBuffer) or
-        (fop, n_bins, CandBuffer, fop32)."""
+        """beams: list of (fop tensor [n_templates][...], n_bins, CandBuffer) or
+        (fop, n_bins, CandBuffer, fop32); a beam's row pitch is its tensor's
+        row stride (a view into a wider plane keeps that plane's pitch)."""
         arr = (hs_beam * max(1, len(beams)))()
         for i, b in enumerate(beams):
             fop, n_bins, cb = b[0], b[1], b[2]
             fop32 = b[3] if len(b) > 3 else None
-            ld = fop.shape[-1]
+            ld = fop.stride(0) if hasattr(fop, "stride") else fop.shape[-1]
             arr[i] = hs_beam(_ptr(fop), _ptr(fop32), int(n_bins), int(ld), cb.c)
         self._keep = list(beams)
         _batch_check(lib().hs_batch_set_beams(self.handle, arr, len(beams),
