@@ -388,6 +388,9 @@ def run_ours(args):
         host = host32.to(lowp).pin_memory()
     fop = host.cuda()
     fop32 = fop if args.dtype == "f32" else host32.cuda()
+    # the plan declares the plane non-negative unless --check-signs: verify
+    # that promise on the whole plane (outside the timed region)
+    nonneg_verified = bool((fop32 >= 0).all().item())
     cands = hs.CandBuffer(1 << 20)
     plan = hs.Plan(nt, n, H, ta, dtype=args.dtype, order=args.order, tile_bins=args.tile_bins,
                    grid_per_sm=args.grid_per_sm or 0, stages=args.stages, z_split=args.z_split,
@@ -551,6 +554,7 @@ def run_ours(args):
                        "p_fa": wl.p_fa, "kernel": plan.kernel, "index": args.index,
                        "inputs": ("checked for negative values" if args.check_signs else
                                   "declared non-negative (powers; plan option assume_nonneg)"),
+                       "inputs_verified_nonneg": nonneg_verified,
                        "tile_bins": plan.tile_bins,
                        "order": args.order, "grid_per_sm": args.grid_per_sm or 0,
                        "candidates": n_cand,

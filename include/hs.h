@@ -86,8 +86,8 @@ typedef struct {
     int z_split;    /* with stages > 0: consumer groups of tile_bins threads (0 = 2) */
     int assume_nonneg; /* 1: the caller declares every plane value non-negative and not
                        NaN (detected power is); the staged kernel then skips its per-value
-                       sign check (about 4 % faster; compiled for 85 x 16 and 21 x 8 at
-                       128 bins).  A plane that breaks the promise may lose candidates.
+                       sign check (a few % faster; every compiled shape at 128 bins).  A
+                       plane that breaks the promise may lose candidates.
                        0 (default): signed inputs are handled exactly. */
 } hs_options;
 
@@ -132,12 +132,21 @@ typedef struct hs_plan hs_plan;
 HS_API hs_status hs_plan_create(hs_plan **out, int n_templates, int64_t n_bins, int H,
                          const float *thresholds, const hs_options *opt);
 
-/* Enqueue harmonic summing + detection of one plane on `stream`.
+/* Enqueue harmonic summing + detection of one plane on `stream`: for every
+ * point (z, f) of the plane and every level k = 1..H, the harmonic-plane
+ * value HP_k(z, f) = sum over m = 1..k of FOP(rho(z, m), floor(f / m)) (the
+ * stretch of Eq. 1 accumulated as in Eq. 2, Section III), tested against the
+ * level's threshold TA(k, z) as Algorithms 1 and 2 detect; every point with
+ * HP_k > TA(k, z) becomes a candidate record (Section III's F, H, B, A
+ * fields), in no particular order.  All levels of a point are formed
+ * together and never stored, the MultipleHP order of Algorithm 2.
  *  fop   : device plane [n_templates][row pitch], row-major, plan dtype,
  *          16-byte aligned; borrowed until the stream passes the kernel.
- *  cands : caller-owned buffer (see hs_cand_buf).
+ *  cands : caller-owned buffer (see hs_cand_buf); its counters are reset on
+ *          `stream` before the kernel.
  * A plan may serve several streams at once if each run has its own cands.
- * Errors: HS_ERR_INVALID (null/misaligned pointers), HS_ERR_CUDA. */
+ * Errors (at enqueue): HS_ERR_INVALID (null/misaligned pointers),
+ * HS_ERR_CUDA; device-side outcomes are read by hs_cand_sync. */
 HS_API hs_status hs_run(hs_plan *plan, const void *fop, hs_stream_t stream,
                  const hs_cand_buf *cands);
 
@@ -151,10 +160,16 @@ HS_API hs_status hs_run(hs_plan *plan, const void *fop, hs_stream_t stream,
 HS_API hs_status hs_run_checked(hs_plan *plan, const void *fop, const float *fop_f32,
                          hs_stream_t stream, const hs_cand_buf *cands);
 
-/* Synchronise `stream`, read the candidate count and device status.
+/* Synchronise `stream`, read the candidate count and device status: the end
+ * of one detection pass of Section III.  The paper keeps at most N_cand
+ * candidates per harmonic plane and leaves open which (Section IV-A); here
+ * every candidate is returned and the true count reported, and a cap can be
+ * applied afterwards with hs_postfilter.
+ *  cands : the buffer a run wrote (device counters, read on `stream`).
  *  n_out : receives the number of candidates found (the true count).
  * Returns HS_ERR_TIMEOUT if a device wait gave up, HS_ERR_OVERFLOW if
- * *n_out > capacity (the first `capacity` records are valid), else HS_OK. */
+ * *n_out > capacity (the first `capacity` records are valid), HS_ERR_CUDA if
+ * the copy or the synchronisation failed, else HS_OK. */
 HS_API hs_status hs_cand_sync(const hs_cand_buf *cands, hs_stream_t stream, uint32_t *n_out);
 
 /* End-to-end call on host memory: copies fop_host (the plane, plan dtype,
@@ -400,9 +415,11 @@ HS_API hs_status hs_run_range(hs_plan *p, const void *fop, const float *fop32, i
  *  - Limit: H * n_templates <= 16384 (a 64 KiB table); larger requests fail
  *    with HS_ERR_INVALID.  Every GPU that loads the library holds the array
  *    until the process exits.
- *  - The first call on a device looks up the array's device address with
- *    that device current (cudaGetSymbolAddress); make that first call before
- *    any stream capture.
+ *  - Every call looks up the array's device address with the caller's
+ *    device current (cudaGetSymbolAddress), so a context made again after
+ *    cudaDeviceReset gets the right one.  The first call on a device may load
+ *    the library's module there: make that first call before any stream
+ *    capture.
  *  - All calls share the array and it keeps the last call's thresholds: two
  *    calls whose work overlaps on the GPU (different streams, or threads)
  *    race on it.  Serialise them, e.g. issue them on one stream.

@@ -10,11 +10,7 @@
 // image instead of a plan allocation, and tiles run in linear order (no
 // order table).
 #include <cmath>
-#include <cstdio>
-#include <mutex>
 #include <string>
-
-#include <cudaTypedefs.h>
 
 #include "hs_internal.h"
 
@@ -28,10 +24,6 @@ constexpr int kNoAllocMaxThresholds = 16384;
 // library holds it until the process exits.  All calls share it.
 __device__ __align__(256) float g_noalloc_ta[kNoAllocMaxThresholds];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-float *g_ta_ptr[kMaxDevices]; // device address of g_noalloc_ta, per device
-
 thread_local std::string g_err;
 
 hs_status fail(hs_status s, const std::string &msg)
@@ -40,44 +32,21 @@ hs_status fail(hs_status s, const std::string &msg)
     return s;
 }
 
-// Device address of the static table on the current device (set-up on the
-// first call per device: the symbol's address is looked up with that device
-// current and cached).
+// Device address of the static table for the current device.  It is looked
+// up on every call, with the caller's device current, so a context made
+// again (after cudaDeviceReset) never receives a stale address; after the
+// first call on a device the lookup is a host-side table read.  The first
+// call on a device may load the library's module there, which is why that
+// call should come before any stream capture.
 hs_status table_address(float **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess)
-        return fail(HS_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices)
-        return fail(HS_ERR_UNSUPPORTED, "device index beyond the static scratch table");
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_ta_ptr[dev]) {
-        void *ptr = nullptr;
-        e = cudaGetSymbolAddress(&ptr, g_noalloc_ta);
-        if (e != cudaSuccess || !ptr)
-            return fail(HS_ERR_CUDA,
-                        std::string("cudaGetSymbolAddress(static thresholds): ") +
-                            cudaGetErrorString(e));
-        g_ta_ptr[dev] = static_cast<float *>(ptr);
-    }
-    *out = g_ta_ptr[dev];
+    void *ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_ta);
+    if (e != cudaSuccess || !ptr)
+        return fail(HS_ERR_CUDA, std::string("cudaGetSymbolAddress(static thresholds): ") +
+                                     cudaGetErrorString(e));
+    *out = static_cast<float *>(ptr);
     return HS_OK;
-}
-
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
-                                             cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    });
-    return fn;
 }
 
 } // namespace
@@ -126,22 +95,13 @@ extern "C" hs_status hs_run_noalloc(int n_templates, int64_t n_bins, int H,
         // prefilter bounds per level group, as a plan computes them
         float tmin[kMaxGroups];
         group_bounds(thresholds, n_templates, H, 0.f, 0.f, tmin);
-        auto fn = encode_fn();
-        if (!fn)
-            return fail(HS_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+        // the plan path's descriptors (host-side encoding, no allocation)
         CUtensorMap maps[kMaxStagedH];
         for (int m = 1; m <= H; ++m) {
             int w = 0, rows = 0;
             staged_box(sh, m, &w, &rows);
-            cuuint64_t dims[2] = {(cuuint64_t)n_bins, (cuuint64_t)n_templates};
-            cuuint64_t strides[1] = {(cuuint64_t)n_bins * 4};
-            cuuint32_t box[2] = {(cuuint32_t)w, (cuuint32_t)rows};
-            cuuint32_t estr[2] = {1, 1};
-            CUresult r = fn(&maps[m - 1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
-                            const_cast<void *>(fop), dims, strides, box, estr,
-                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (r != CUDA_SUCCESS)
+            if (encode_tensor_map(&maps[m - 1], HS_F32, fop, n_bins, n_bins, n_templates, w,
+                                  rows) != CUDA_SUCCESS)
                 return fail(HS_ERR_CUDA, "cuTensorMapEncodeTiled failed");
         }
         StagedLaunch L{};

@@ -70,3 +70,22 @@ def test_noalloc_rejects_tables_beyond_its_limit():
     cands = hs.CandBuffer(16)
     with pytest.raises(hs.HsError, match="16384"):
         hs.hs_run_noalloc(nt, 64, H, np.ones((H, nt), np.float32), plane_d, None, cands.c)
+
+
+def test_noalloc_leaves_free_device_memory_unchanged():
+    # the property the entry point exists for: after a first call on each
+    # path (staged and generic), further calls change no device allocation
+    cases = [(21, 65536, 8), (9, 3001, 6)]  # staged kernel; generic fallback
+    planes = {c: torch.from_numpy(synth.noise(c[0], c[1], seed=77)).cuda() for c in cases}
+    tas = {c: synth.thresholds(1e-3, c[2], c[0]) for c in cases}
+    cands = hs.CandBuffer(1 << 16)
+    for c in cases:
+        _noalloc(planes[c], tas[c], c[0], c[1], c[2], cands)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(5):
+        for c in cases:
+            hs.hs_run_noalloc(c[0], c[1], c[2], tas[c], planes[c], None, cands.c)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
