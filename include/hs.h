@@ -58,7 +58,9 @@ typedef enum {
     HS_ERR_OVERFLOW = 4,    /* more candidates than the buffer holds */
     HS_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
     HS_ERR_UNSUPPORTED = 6, /* valid request this build does not implement */
-    HS_ERR_BUSY = 7         /* serving engine: queue full, or result not ready in time */
+    HS_ERR_BUSY = 7,        /* serving engine: queue full, or result not ready in time */
+    HS_ERR_BOUNDS = 8       /* a library built with -DHS_CHECK_BOUNDS found an index outside
+                               its buffer (the access was skipped); never in a normal build */
 } hs_status;
 
 typedef enum { HS_F32 = 0, HS_BF16 = 1, HS_F16 = 2 } hs_dtype;

@@ -368,6 +368,7 @@ const char *hs_status_str(hs_status s)
     case HS_ERR_TIMEOUT: return "device wait timed out";
     case HS_ERR_UNSUPPORTED: return "unsupported";
     case HS_ERR_BUSY: return "busy (queue full or not finished)";
+    case HS_ERR_BOUNDS: return "index outside its buffer (bounds-checking build)";
     }
     return "unknown status";
 }

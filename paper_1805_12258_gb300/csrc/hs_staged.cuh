@@ -160,6 +160,18 @@ struct Params {
     int nt_rt;              // templates of the plane (<= NT; kernels with runtime rows)
 };
 
+// Opt-in bounds checks (-DHS_CHECK_BOUNDS).  A checked build tests every
+// shared-memory read of the walk and the exact pass against its own level's
+// span in the stage (and each thread's column against the span's width), and
+// every global read of the exact pass against its threshold table or plane;
+// an index outside sets HS_ERR_BOUNDS in the status word and the read is
+// skipped (0 for a value, +inf for a threshold).  Never a trap.
+#ifdef HS_CHECK_BOUNDS
+constexpr bool kCheckBounds = true;
+#else
+constexpr bool kCheckBounds = false;
+#endif
+
 // Pairwise (tree) sum of cur[LO..HI] with packed adds; depth log2(HI-LO+1).
 template <int LO, int HI, int N>
 __device__ __forceinline__ float2 tree_sum(const float2 (&cur)[N])
@@ -270,7 +282,44 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
         constexpr int m = M + 1;
         const int col = f / m - ((f0 / m) & ~(C::ALIGN - 1));
         bidx[M] = C::OFF(m) / C::ES + C::R(m) * C::W(m) + col;
+        if constexpr (kCheckBounds) {
+            if (col < 0 || col >= C::W(m))
+                set_status(tt.counters, HS_ERR_BOUNDS);
+        }
     });
+    // level m's value at element idx of the stage (checked builds: inside
+    // level m's own span, else skipped)
+    auto sld = [&](auto M, int idx) -> float {
+        if constexpr (kCheckBounds) {
+            constexpr int m = decltype(M)::value + 1;
+            constexpr int lo = C::OFF(m) / C::ES, hi = lo + C::ROWS(m) * C::W(m);
+            if (idx < lo || idx >= hi) {
+                set_status(tt.counters, HS_ERR_BOUNDS);
+                return 0.f;
+            }
+        }
+        return to_f32(sm[idx]);
+    };
+    // threshold of level M + 1 for row z (checked builds: inside the table)
+    auto thr_of = [&](auto M, int z) -> float {
+        if constexpr (kCheckBounds) {
+            if (z + zr < 0 || z + zr >= ntr) {
+                set_status(tt.counters, HS_ERR_BOUNDS);
+                return __int_as_float(0x7f800000);
+            }
+        }
+        return __ldg(p.ta + decltype(M)::value * ntr + (z + zr));
+    };
+    // the FP32 copy at (row rho of the plane's centre-relative rows, bin b)
+    auto copy_at = [&](int rho, int b) -> float {
+        if constexpr (kCheckBounds) {
+            if (rho + zr < 0 || rho + zr >= ntr || b < 0 || (long long)b >= tt.n) {
+                set_status(tt.counters, HS_ERR_BOUNDS);
+                return 0.f;
+            }
+        }
+        return __ldg(tt.fop32 + (long long)(rho + zr) * tt.ld + b);
+    };
 
     // ---- slow pass (defined here, run below): exact per-level test -----------
     // scan(z, write, slot): level sums of row z in Eq. 2 order; returns the hit
@@ -279,7 +328,7 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
         float acc = 0.f, ab = 0.f;
         uint32_t hits = 0u;
         float thr[H];
-        static_for<0, H>([&](auto M) { thr[M] = __ldg(p.ta + M * ntr + (z + zr)); });
+        static_for<0, H>([&](auto M) { thr[M] = thr_of(M, z); });
         // The decision of Section III: HP_k(z, f) > TA(k, z), HP_k formed in
         // the order of Eq. 2 (ascending m) in FP32.  The pass is rare, so
         // what it costs is its code run cold from the instruction cache; the
@@ -289,7 +338,7 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
             static_for<0, H>([&](auto M) {
                 constexpr int m = M + 1;
                 const int rho = z >= 0 ? z / m : -((-z) / m);
-                const float v = to_f32(sm[bidx[M] + rho * C::W(m)]);
+                const float v = sld(M, bidx[M] + rho * C::W(m));
                 acc = (m == 1) ? v : acc + v;
                 if (acc > thr[M]) {
                     hits |= 1u << M;
@@ -308,7 +357,7 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
             static_for<0, H>([&](auto M) {
                 constexpr int m = M + 1;
                 const int rho = z >= 0 ? z / m : -((-z) / m);
-                const float v = to_f32(sm[bidx[M] + rho * C::W(m)]);
+                const float v = sld(M, bidx[M] + rho * C::W(m));
                 acc = (m == 1) ? v : acc + v;
                 ab += fabsf(v);
                 pw[M] = acc;
@@ -326,7 +375,7 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
                 static_for<0, H>([&](auto M) {
                     constexpr int m = M + 1;
                     const int rho = z >= 0 ? z / m : -((-z) / m);
-                    w[M] = __ldg(tt.fop32 + (long long)(rho + zr) * tt.ld + f / m);
+                    w[M] = copy_at(rho, f / m);
                 });
                 float c = 0.f;
                 static_for<0, H>([&](auto M) {
@@ -355,12 +404,12 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
         float acc = 0.f;
         uint32_t hits = 0u;
         float thr[H];
-        static_for<0, H>([&](auto M) { thr[M] = __ldg(p.ta + M * ntr + (z + zr)); });
+        static_for<0, H>([&](auto M) { thr[M] = thr_of(M, z); });
         static_for<0, H>([&](auto M) {
             constexpr int m = M + 1;
             const int rho = z >= 0 ? z / m : -((-z) / m);
-            acc = (m == 1) ? to_f32(sm[bidx[M] + rho * C::W(m)])
-                           : acc + to_f32(sm[bidx[M] + rho * C::W(m)]);
+            acc = (m == 1) ? sld(M, bidx[M] + rho * C::W(m))
+                           : acc + sld(M, bidx[M] + rho * C::W(m));
             pw[M] = acc;
             hits |= (acc > thr[M] ? 1u : 0u) << M;
         });
@@ -458,7 +507,7 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
     if (ok) {
         // template z = 0: every stretch reads the centre row
         static_for<0, H>([&](auto M) {
-            const float v = to_f32(sm[bidx[M]]);
+            const float v = sld(M, bidx[M]);
             put(M, v, v);
             if constexpr (SIGNCHK)
                 negbits |= __float_as_uint(v);
@@ -492,8 +541,8 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
                 constexpr int m = M + 1;
                 if constexpr (zz % m == 0) {
                     constexpr int off = (zz / m) * C::W(m);
-                    const float tv = to_f32(sm[bidx[M] + off]);
-                    const float bv = to_f32(sm[bidx[M] - off]);
+                    const float tv = sld(M, bidx[M] + off);
+                    const float bv = sld(M, bidx[M] - off);
                     put(M, tv, bv);
                     if constexpr (SIGNCHK)
                         negbits |= __float_as_uint(tv) | __float_as_uint(bv);

@@ -17,11 +17,13 @@ import re
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libhs.so")
+# $HS_LIBRARY selects another build of the library (the bounds-checking one,
+# in its tests); a path that does not exist fails loudly like a missing build
+LIB_PATH = os.environ.get("HS_LIBRARY") or os.path.join(_HERE, "libhs.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "hs.h")
 
 HS_OK, HS_ERR_INVALID, HS_ERR_CUDA, HS_ERR_OOM, HS_ERR_OVERFLOW, HS_ERR_TIMEOUT, \
-    HS_ERR_UNSUPPORTED, HS_ERR_BUSY = range(8)
+    HS_ERR_UNSUPPORTED, HS_ERR_BUSY, HS_ERR_BOUNDS = range(9)
 HS_F32, HS_BF16, HS_F16 = 0, 1, 2
 HS_INDEX_STRETCH, HS_INDEX_HFRAC = 0, 1
 HS_ZROUND_SYMMETRIC, HS_ZROUND_FLOOR = 0, 1

@@ -123,3 +123,4 @@ def test_server_and_generator_validate_before_touching_the_device(L):
     assert L.hs_server_submit(None, None, None) == hs.HS_ERR_INVALID
     assert L.hs_server_destroy(None) == hs.HS_OK
     assert "busy" in hs.hs_status_str(hs.HS_ERR_BUSY)
+    assert "bounds" in hs.hs_status_str(hs.HS_ERR_BOUNDS)
