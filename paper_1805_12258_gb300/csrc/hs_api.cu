@@ -33,6 +33,7 @@ struct hs_plan {
     float band_abs = 0.f;  // absolute error bound (FP16 subnormals)
     std::vector<float> ta;   // [H][nt]
     std::vector<float> tmin; // [groups]: min over rows and the group's levels
+    std::vector<float> lmin; // [H]: per level the smallest threshold over all rows
     float *d_ta = nullptr;
     uint32_t *d_order = nullptr;
     std::mutex mu;                 // guards the descriptor cache and streams
@@ -314,6 +315,7 @@ hs_status launch_range(hs_plan *p, const void *fop, const float *fop32, cudaStre
         a.cap = c->capacity;
         a.f_lo = f_lo;
         a.f_hi = f_hi;
+        a.lmin = p->lmin.data();
         e = launch_generic(a, s);
         if (e != cudaSuccess)
             return cuda_fail(e, "generic kernel launch");
@@ -416,6 +418,10 @@ hs_status hs_plan_create(hs_plan **out, int n_templates, int64_t n_bins, int H,
     p->opt = o;
     cudaGetDevice(&p->device);
     p->ta.assign(thresholds, thresholds + (size_t)H * n_templates);
+    p->lmin.assign((size_t)H, INFINITY);
+    for (int k = 0; k < H; ++k)
+        for (int r = 0; r < n_templates; ++r)
+            p->lmin[(size_t)k] = std::min(p->lmin[(size_t)k], p->ta[(size_t)k * n_templates + r]);
     storage_error(o.dtype, H, &p->delta, &p->band_abs);
 
     // kernel choice: the staged kernel needs a compiled shape, the paper's

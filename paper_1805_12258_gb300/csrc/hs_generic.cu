@@ -315,6 +315,8 @@ cudaError_t launch_generic(const GenericArgs &a, cudaStream_t s)
 {
     if (a.f_hi <= a.f_lo)
         return cudaSuccess;
+    if (hfrac_pairs_available(a))
+        return launch_hfrac_pairs(a, a.lmin, s);
     const int threads = 128;
     const long long nbins = a.f_hi - a.f_lo;
     const long long bx = (nbins + threads - 1) / threads;

@@ -33,9 +33,15 @@ struct GenericArgs {
     uint32_t *counters;   // [0] count, [1] status
     uint32_t cap;         // record capacity
     long long f_lo, f_hi; // bin range of this launch
+    const float *lmin;    // host: per level the smallest threshold over all rows (H
+                          // values), a prefilter bound; null = test every row exactly
 };
 
 cudaError_t launch_generic(const GenericArgs &a, cudaStream_t s);
+// The harmonic-fraction map's pair-walk kernel (hs_hfrac.cu): FP32 planes,
+// symmetric rounding, H = 8 or 16.
+bool hfrac_pairs_available(const GenericArgs &a);
+cudaError_t launch_hfrac_pairs(const GenericArgs &a, const float *lmin_host, cudaStream_t s);
 
 // Staged (TMA) kernel: one CTA per tile of TB bins x all templates.
 constexpr int kMaxStagedH = 16;
