@@ -165,22 +165,23 @@ class ClockSampler:
 
 # ---- CPU oracle leg --------------------------------------------------------------
 
-def oracle_sample(plane, ta, H, cpu_seconds, threads):
+def oracle_sample(plane, ta, H, cpu_seconds, threads, index="stretch"):
     """Time the FP64 oracle on all rows x a bin window; returns a dict."""
     import oracle
     oracle.build()
+    idx = oracle.HFRAC if index == "hfrac" else oracle.STRETCH
     nt, n = plane.shape
     # calibrate: per-point cost on a small window, one thread
     cal = 2048
     t0 = time.perf_counter()
-    oracle.detect(plane, H, ta, f_lo=n // 2, f_hi=n // 2 + cal, threads=1)
+    oracle.detect(plane, H, ta, index=idx, f_lo=n // 2, f_hi=n // 2 + cal, threads=1)
     per_point = (time.perf_counter() - t0) / (nt * cal)
-    # bins [n - bins, n): the high bins, whose stretch reads span the plane
+    # bins [n - bins, n): the high bins, whose reads span the plane
     bins = int(cpu_seconds / max(per_point, 1e-12) / nt)
     bins = max(min(n, threads * 64), min(bins, n))
     lo = n - bins
     t0 = time.perf_counter()
-    cands, near = oracle.detect(plane, H, ta, f_lo=lo, f_hi=n, threads=threads)
+    cands, near = oracle.detect(plane, H, ta, index=idx, f_lo=lo, f_hi=n, threads=threads)
     dt = time.perf_counter() - t0
     what = "the whole plane" if bins == n else f"bins [{lo}, {n}) of the same plane"
     return {"value": nt * bins / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
@@ -356,6 +357,47 @@ def precision_summary(fop32, ta, H, ref_records, nonneg, steps=500):
     return out
 
 
+def hfrac_summary(fop32, ta, H, stretch_us, steps=20):
+    """The harmonic-fraction index map (level k sums the terms h/k, h = 1..k)
+    on the same plane: its staged kernels' mean time per run (plan events,
+    one launch per level family), throughput, the ratio to the stretch map's
+    kernel time, and its records (returned beside the summary)."""
+    import torch
+
+    from paper_1805_12258_gb300 import hs
+    nt, n = fop32.shape
+    stream = torch.cuda.current_stream()
+    peak, kind = peaks()
+    c = hs.CandBuffer(1 << 20)
+    with hs.Plan(nt, n, H, ta, index="hfrac") as plan:
+        for _ in range(3):
+            plan.run(fop32, c, stream)
+        torch.cuda.synchronize()
+        clocks = ClockSampler(torch.cuda.current_device())
+        clocks.start()
+        time.sleep(0.3)
+        plan.set_timing(True)
+        plan.kernel_time()
+        for _ in range(steps):
+            plan.run(fop32, c, stream)
+        launches = hs.hs_last_launch_count()
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        ms, k = plan.kernel_time()
+        plan.set_timing(False)
+        recs, cnt, st = c.fetch(stream)
+        kernel, tb = plan.kernel, plan.tile_bins
+    us = ms / max(k, 1) * 1e3
+    algo = nt * n * 4 + H * nt * 4 + 16 * int(cnt) + 8
+    return {"index": "hfrac", "kernel": kernel, "tile_bins": tb, "launches_per_run": launches,
+            "mean_us_per_run": us, "points_per_s": nt * n / (us / 1e6),
+            "level_sums_per_s": nt * n * H / (us / 1e6), "time_vs_stretch_map": us / stretch_us,
+            "candidates": int(cnt), "status": hs.hs_status_str(st),
+            "effective_hbm_gbs": algo / (us / 1e6) / 1e9,
+            "frac_of_peak_on_unique_bytes": algo / (us / 1e6) / 1e9 / peak,
+            "peak_kind": f"{kind} copy bandwidth", "clocks": clk}, recs
+
+
 # ---- our arm ------------------------------------------------------------------------
 
 def run_ours(args):
@@ -494,6 +536,9 @@ def run_ours(args):
     kname = (f"staged {nt}x{n} H={H} {args.dtype} tb={plan.tile_bins} "
              f"order={ORDER_NAMES.get(args.order, args.order)}"
              if plan.kernel == "staged" else f"generic {nt}x{n} H={H} {args.dtype} {args.index}")
+    if args.index == "hfrac" and plan.kernel == "staged":
+        kname = (f"staged hfrac {nt}x{n} H={H} {args.dtype} tb={plan.tile_bins} "
+                 "(one launch per level family; time per run)")
 
     # e2e through hs_run_host: pinned host plane -> device, sum, records -> host
     e2e = None
@@ -525,16 +570,19 @@ def run_ours(args):
             e2e["recheck"] = "FP32 copy read in place from page-locked host memory"
         del dev
 
-    cpu, parity = None, None
+    extras = (rank == 0 and ws == 1 and not args.no_extras and args.workload == "ska" and
+              args.dtype == "f32" and args.index == "stretch" and not band)
+    cpu, parity, cpu_hfrac = None, None, None
     if rank == 0 and not args.no_cpu:
-        cpu = oracle_sample(plane_np, ta, H, args.cpu_seconds, host_cores())
-        if not band and args.index == "stretch":
+        cpu = oracle_sample(plane_np, ta, H, args.cpu_seconds, host_cores(), index=args.index)
+        if not band:
             parity = window_parity(timed_records, cpu)
         cpu = {k: v for k, v in cpu.items() if not k.startswith("_")}
+        if extras:  # a short oracle window for the harmonic-fraction section
+            cpu_hfrac = oracle_sample(plane_np, ta, H, 3.0, host_cores(), index="hfrac")
 
     sections = {}
-    if (rank == 0 and ws == 1 and not args.no_extras and args.workload == "ska" and
-            args.dtype == "f32" and args.index == "stretch" and not band):
+    if extras:
         # the other forms of the method, each measured on its own after the
         # main measurement: 16-bit storage of this plane, the 64-beam batch,
         # a short serving run
@@ -544,6 +592,12 @@ def run_ours(args):
         torch.cuda.empty_cache()
         sections["serve"] = serve_summary(args, seconds=2.0, rate=1000.0, closed_k=1000)
         torch.cuda.empty_cache()
+        hf, hf_recs = hfrac_summary(fop, ta, H, mean_kernel_s * 1e6)
+        if cpu_hfrac is not None:
+            hf["parity_window"] = window_parity(hf_recs, cpu_hfrac)
+            hf["parity_in_window"] = hf["parity_window"]["equal"]
+            hf["cpu_oracle_points_per_s"] = cpu_hfrac["value"]
+        sections["hfrac"] = hf
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -580,6 +634,7 @@ def run_ours(args):
             "precision": precision if precision is not None else sections.get("precision"),
             "batch": sections.get("batch"),
             "serve": sections.get("serve"),
+            "hfrac": sections.get("hfrac"),
             "parity_in_window": None if parity is None else parity["equal"],
             "parity_window": parity,
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,

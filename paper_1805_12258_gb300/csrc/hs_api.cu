@@ -266,7 +266,28 @@ hs_status launch_range(hs_plan *p, const void *fop, const float *fop32, cudaStre
         ev_stop = p->tev[p->tev_used + 1];
         p->tev_used += 2;
     }
-    if (p->kernel == HS_KERNEL_STAGED) {
+    int launches = 1;
+    if (p->kernel == HS_KERNEL_STAGED && p->opt.index == HS_INDEX_HFRAC) {
+        HfracStagedLaunch L{};
+        L.fop = fop;
+        L.nt = p->nt;
+        L.n = p->n;
+        L.ld = p->ld;
+        L.H = p->H;
+        L.tb = p->tb;
+        L.ta = p->d_ta;
+        L.lmin = p->lmin.data();
+        L.rec = c->records;
+        L.counters = c->count;
+        L.cap = c->capacity;
+        L.f_lo = f_lo;
+        L.f_hi = f_hi;
+        L.order = full ? p->d_order : nullptr;
+        launches = 0;
+        e = launch_hfrac_staged(L, s, &launches);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "harmonic-fraction staged kernel launch");
+    } else if (p->kernel == HS_KERNEL_STAGED) {
         hs_status st = encode_maps(p, fop);
         if (st != HS_OK)
             return st;
@@ -320,7 +341,7 @@ hs_status launch_range(hs_plan *p, const void *fop, const float *fop32, cudaStre
         if (e != cudaSuccess)
             return cuda_fail(e, "generic kernel launch");
     }
-    ++g_last_launches;
+    g_last_launches += launches;
     if (ev_stop) {
         e = cudaEventRecord(ev_stop, s);
         if (e != cudaSuccess)
@@ -427,10 +448,21 @@ hs_status hs_plan_create(hs_plan **out, int n_templates, int64_t n_bins, int H,
     // kernel choice: the staged kernel needs a compiled shape, the paper's
     // index map with symmetric rounding, and 16-byte aligned rows for TMA
     const size_t es = elem_size(o.dtype);
-    p->tb = o.tile_bins ? o.tile_bins : 128;
+    p->tb = o.tile_bins ? o.tile_bins : o.index == HS_INDEX_HFRAC ? 64 : 128;
     const StagedShape sh{n_templates, H, p->tb, o.dtype};
-    const bool staged_ok = staged_available(sh) && o.index == HS_INDEX_STRETCH &&
-                           o.zround == HS_ZROUND_SYMMETRIC && (p->ld * (long long)es) % 16 == 0;
+    const bool staged_ok =
+        o.index == HS_INDEX_HFRAC
+            ? hfrac_staged_available(n_templates, n_bins, p->ld, H, o.dtype, o.index, o.zround,
+                                     p->tb)
+            : staged_available(sh) && o.zround == HS_ZROUND_SYMMETRIC &&
+                  (p->ld * (long long)es) % 16 == 0;
+    if (o.kernel == HS_KERNEL_STAGED && !staged_ok && o.index == HS_INDEX_HFRAC) {
+        delete p;
+        return fail(HS_ERR_UNSUPPORTED, "no staged kernel for the harmonic-fraction map with "
+                                        "these options (compiled: FP32, symmetric rounding, "
+                                        "H = 8 or 16, 64 or 128 tile bins, rows a multiple "
+                                        "of 16 bytes)");
+    }
     if (o.kernel == HS_KERNEL_STAGED && !staged_ok) {
         delete p;
         return fail(HS_ERR_UNSUPPORTED, "no staged kernel for this shape/options "
@@ -444,6 +476,11 @@ hs_status hs_plan_create(hs_plan **out, int n_templates, int64_t n_bins, int H,
         p->tb = 128;
     } else {
         p->kernel = HS_KERNEL_STAGED;
+        if (o.stages > 0 && o.index == HS_INDEX_HFRAC) {
+            delete p;
+            return fail(HS_ERR_UNSUPPORTED, "the harmonic-fraction map has no pipelined "
+                                            "staged kernel");
+        }
         if (o.stages > 0) {
             const int zs = o.z_split ? o.z_split : 2;
             if (!ring_available(sh, zs, o.stages)) {
@@ -474,7 +511,8 @@ hs_status hs_plan_create(hs_plan **out, int n_templates, int64_t n_bins, int H,
         p->groups = group_bounds(p->ta.data(), n_templates, H, p->delta, p->band_abs,
                                  p->tmin.data());
         p->n_tiles = (int)((n_bins + p->tb - 1) / p->tb);
-        const int kind = o.order == 0 ? 3 : o.order; // default: semitone
+        // default: semitone (the harmonic-fraction map: linear)
+        const int kind = o.order != 0 ? o.order : o.index == HS_INDEX_HFRAC ? 1 : 3;
         std::vector<uint32_t> ord = tile_order(p->n_tiles, kind);
         e = cudaMalloc(&p->d_order, sizeof(uint32_t) * ord.size());
         if (e == cudaSuccess)

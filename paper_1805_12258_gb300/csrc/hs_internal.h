@@ -43,6 +43,26 @@ cudaError_t launch_generic(const GenericArgs &a, cudaStream_t s);
 bool hfrac_pairs_available(const GenericArgs &a);
 cudaError_t launch_hfrac_pairs(const GenericArgs &a, const float *lmin_host, cudaStream_t s);
 
+// The harmonic-fraction map's staged (TMA) kernel (hs_hfrac.cu): one launch
+// per level family, tiles of tb bins by K row pairs.
+struct HfracStagedLaunch {
+    const void *fop;       // FP32 plane [nt][ld], 16-byte aligned
+    int nt;                // templates (odd)
+    long long n, ld;       // bins, row pitch (elements, a multiple of 4)
+    int H, tb;             // levels (8 or 16), tile bins (64 or 128)
+    const float *ta;       // device thresholds [H][nt]
+    const float *lmin;     // host: per level the smallest threshold over all rows
+    hs_cand *rec;
+    uint32_t *counters;
+    uint32_t cap;
+    long long f_lo, f_hi;  // bin range of this launch
+    const uint32_t *order; // device tile order over the plane's tiles, or null
+};
+bool hfrac_staged_available(int nt, long long n, long long ld, int H, int dtype, int index,
+                            int zround, int tb);
+// Adds the number of kernels launched to *launches.
+cudaError_t launch_hfrac_staged(const HfracStagedLaunch &L, cudaStream_t s, int *launches);
+
 // Staged (TMA) kernel: one CTA per tile of TB bins x all templates.
 constexpr int kMaxStagedH = 16;
 constexpr int kMaxGroups = 8;

@@ -106,14 +106,72 @@ def test_every_level_sum(nt, n, H, kernel):
 @pytest.mark.parametrize("index,zround", [("hfrac", "symmetric"), ("stretch", "floor"),
                                           ("hfrac", "floor")])
 def test_other_index_maps(index, zround, nt, n, H):
-    # H = 8 and 16 run the generic kernel's compile-time variant (harmonic
-    # fractions grouped into families that share loads), H = 13 the runtime one
+    # The harmonic-fraction map with symmetric rounding at H = 8 or 16 runs
+    # the staged kernel when rows are a multiple of 16 bytes and the gather
+    # pair kernel otherwise (21 x 777); H = 13 and floor rounding run the
+    # generic kernel
     plane = synth.noise(nt, n, seed=5)
     got, used = _all_sums(plane, H, index=index, zround=zround)
-    assert used == "generic"
+    staged = index == "hfrac" and zround == "symmetric" and H in (8, 16) and n % 4 == 0
+    assert used == ("staged" if staged else "generic")
     ref = oracle.planes(plane, H, index=oracle.HFRAC if index == "hfrac" else oracle.STRETCH,
                         zround=oracle.ZFLOOR if zround == "floor" else oracle.ZSYM)
     np.testing.assert_allclose(got, ref, rtol=RTOL, atol=0)
+
+
+# --- the harmonic-fraction map: staged (TMA) and gather kernels ------------------
+
+@pytest.mark.parametrize("nt,n,H,tb", [(85, 1000, 16, 128), (85, 1000, 16, 64),
+                                       (21, 776, 8, 128), (21, 776, 8, 64),
+                                       (127, 520, 16, 128), (1, 300, 16, 128), (3, 64, 8, 64),
+                                       (9, 4, 16, 128), (33, 2052, 8, 128), (43, 1300, 16, 64)])
+def test_hfrac_staged_every_level_sum(nt, n, H, tb):
+    # Row blocks of K pairs (the last one partial for every family head K
+    # that does not divide the pair count), ragged last tiles, one template,
+    # a plane narrower than a box
+    plane = synth.noise(nt, n, seed=nt * 31 + n + tb)
+    got, used = _all_sums(plane, H, index="hfrac", tile_bins=tb)
+    assert used == "staged"
+    ref = oracle.planes(plane, H, index=oracle.HFRAC)
+    np.testing.assert_allclose(got, ref, rtol=RTOL, atol=0)
+
+
+@pytest.mark.parametrize("nt,n,H", [(85, 1000, 16), (21, 777, 8), (127, 333, 16), (1, 50, 8)])
+def test_hfrac_gather_every_level_sum(nt, n, H):
+    # the gather pair kernel: forced, or for rows that are not 16-byte multiples
+    plane = synth.noise(nt, n, seed=nt * 37 + n)
+    got, used = _all_sums(plane, H, index="hfrac", kernel="generic")
+    assert used == "generic"
+    ref = oracle.planes(plane, H, index=oracle.HFRAC)
+    np.testing.assert_allclose(got, ref, rtol=RTOL, atol=0)
+
+
+def test_hfrac_kernels_orders_and_ranges_agree():
+    # staged (linear and semitone tile order, 64 and 128 bins), gather and a
+    # run split into two tile-aligned ranges give the same records, which
+    # are the oracle's candidates
+    nt, n, H = 85, 30000, 16
+    plane = synth.noise(nt, n, seed=71)
+    ta = synth.thresholds(1e-4, H, nt)
+    runs = [dict(index="hfrac"), dict(index="hfrac", order=3), dict(index="hfrac", tile_bins=64),
+            dict(index="hfrac", kernel="generic")]
+    results = []
+    for kw in runs:
+        recs, cnt, st, _ = run_gpu(plane, H, ta, **kw)
+        assert st == hs.HS_OK and cnt > 0
+        results.append(np.sort(recs, order=["k", "z", "bin"]))
+    fop = torch.from_numpy(plane).cuda()
+    cands = hs.CandBuffer(1 << 20)
+    with hs.Plan(nt, n, H, ta, index="hfrac") as plan:
+        plan.run_range(fop, cands, 0, 128 * 100)
+        plan.run_range(fop, cands, 128 * 100, n, append=True)
+        recs, cnt, st = cands.fetch()
+    assert st == hs.HS_OK
+    results.append(np.sort(recs, order=["k", "z", "bin"]))
+    for r in results[1:]:
+        assert np.array_equal(r, results[0])
+    ref, near = oracle.detect(plane, H, ta, index=oracle.HFRAC, threads=8)
+    assert_matches_oracle(results[0], ref, near)
 
 
 @pytest.mark.parametrize("nt,n,H,dtype", [(85, 20000, 16, "f32"), (21, 50000, 8, "f32"),
@@ -508,6 +566,29 @@ def test_ska_plane_row_sums(ska, z, assume_nonneg):
     f = np.arange(wl.n_bins, dtype=np.int64)
     ref = oracle.sample(plane, wl.H, np.full(wl.n_bins, z, np.int32), f)
     np.testing.assert_allclose(got, ref, rtol=RTOL, atol=0)
+
+
+def test_ska_plane_hfrac_candidates(ska):
+    # The harmonic-fraction map on the full plane: every record's power
+    # against the oracle's level sum at that point; inside three bin windows
+    # (the start, the middle and the end of the plane) the record set is the
+    # oracle's; the gather kernel gives the same records as the staged one
+    wl, plane, ta = ska
+    recs, n, st, used = run_gpu(plane, wl.H, ta, index="hfrac")
+    assert used == "staged" and st == hs.HS_OK and n == len(recs) and n > 1000
+    ref = oracle.sample(plane, wl.H, recs["z"].astype(np.int32), recs["bin"].astype(np.int64),
+                        index=oracle.HFRAC)[np.arange(n), recs["k"].astype(int) - 1]
+    np.testing.assert_allclose(recs["power"], ref, rtol=RTOL, atol=0)
+    for lo in (0, wl.n_bins // 2 - 6000, wl.n_bins - 12000):
+        hi = lo + 12000
+        win = recs[(recs["bin"] >= lo) & (recs["bin"] < hi)]
+        o, near = oracle.detect(plane, wl.H, ta, index=oracle.HFRAC, f_lo=lo, f_hi=hi,
+                                threads=8)
+        assert_matches_oracle(win, o, near)
+    g, ng, st2, used2 = run_gpu(plane, wl.H, ta, index="hfrac", kernel="generic")
+    assert used2 == "generic" and st2 == hs.HS_OK and ng == n
+    assert np.array_equal(np.sort(g, order=["k", "z", "bin"]),
+                          np.sort(recs, order=["k", "z", "bin"]))
 
 
 # --- other plane shapes: kernel families with runtime rows ------------------------
