@@ -69,6 +69,17 @@ constexpr int head_at(int i, int H)
 }
 constexpr int round_up(int x, int a) { return (x + a - 1) / a * a; }
 
+// Opt-in bounds checks (-DHS_CHECK_BOUNDS): the staged kernel tests every
+// shared-memory read against its own term's box and the gather kernel every
+// plane read against the plane, each threshold read against the table; an
+// index outside sets HS_ERR_BOUNDS in the status word and the read is skipped
+// (0 for a value, +inf for a threshold).  Never a trap.
+#ifdef HS_CHECK_BOUNDS
+constexpr bool kCheck = true;
+#else
+constexpr bool kCheck = false;
+#endif
+
 // Host counterpart of static_for: f(std::integral_constant<int, i>) for
 // i = B .. E-1.
 template <int B, int E, typename F>
@@ -128,8 +139,14 @@ __device__ __forceinline__ void family_levels(const float2 (&t)[K], int zz, unsi
             constexpr int k = Kk;
             if constexpr (K % k == 0 && fam_of(k, H) == K) {
                 const float2 s = lv[k - 1];
-                const float tt = __ldg(o.ta + (k - 1) * o.nt + (Z + zz));
-                const float tb = __ldg(o.ta + (k - 1) * o.nt + (Z - zz));
+                float tt, tb;
+                if (kCheck && (zz < 0 || zz > Z)) {
+                    set_status(o.counters, HS_ERR_BOUNDS);
+                    tt = tb = __int_as_float(0x7f800000);
+                } else {
+                    tt = __ldg(o.ta + (k - 1) * o.nt + (Z + zz));
+                    tb = __ldg(o.ta + (k - 1) * o.nt + (Z - zz));
+                }
                 ht |= (s.x > tt ? 1u : 0u) << (k - 1);
                 hb |= (zz > 0 && s.y > tb ? 1u : 0u) << (k - 1);
             }
@@ -253,10 +270,16 @@ __global__ void __launch_bounds__(TB *ZG, 1024 / (TB * ZG)) hfrac_staged_kernel(
             static_for<0, 4>([&](auto Cc) {
                 constexpr int h = 4 * q + Cc + 1;
                 if constexpr (h <= K) {
-                    t[h - 1].x = *reinterpret_cast<const float *>(smem + G::TOP(h) +
-                                                                  (col[h - 1] + o[Cc]));
-                    t[h - 1].y = *reinterpret_cast<const float *>(
-                        smem + (G::BOT(h) + (h - 1) * G::W(h) * 4) + (col[h - 1] - o[Cc]));
+                    const int at = G::TOP(h) + col[h - 1] + o[Cc];
+                    const int ab = G::BOT(h) + (h - 1) * G::W(h) * 4 + col[h - 1] - o[Cc];
+                    if (kCheck && (at < G::TOP(h) || at >= G::TOP(h) + G::BOX(h) ||
+                                   ab < G::BOT(h) || ab >= G::BOT(h) + G::BOX(h))) {
+                        set_status(p.o.counters, HS_ERR_BOUNDS);
+                        t[h - 1] = make_float2(0.f, 0.f);
+                    } else {
+                        t[h - 1].x = *reinterpret_cast<const float *>(smem + at);
+                        t[h - 1].y = *reinterpret_cast<const float *>(smem + ab);
+                    }
                 }
             });
         });
@@ -375,6 +398,10 @@ __device__ __forceinline__ void gather_family(const GenericArgs &a, const LevelB
     __syncthreads();
 
     const HitSink o{a.ta, a.rec, a.counters, a.cap, a.nt};
+    const char *plane_lo = static_cast<const char *>(a.fop);
+    const char *plane_hi =
+        plane_lo + ((long long)(a.nt - 1) * a.ld + a.n) * (long long)sizeof(float);
+    uint32_t *a_counters = a.counters;
     // this family's bin offsets in the centre row, once per thread
     const char *pc = reinterpret_cast<const char *>(static_cast<const float *>(a.fop) +
                                                     (long long)Z * a.ld);
@@ -386,15 +413,20 @@ __device__ __forceinline__ void gather_family(const GenericArgs &a, const LevelB
     for (int zl = 0; zl < n_zz; ++zl) { // uniform over the CTA
         const longlong2 *d2 = reinterpret_cast<const longlong2 *>(s_off + zl * KP);
         float2 t[K];
+        // plane value at byte address a (checked builds: inside the plane)
+        auto ld = [&](const char *a) -> float {
+            if (kCheck && (a < plane_lo || a >= plane_hi)) {
+                set_status(a_counters, HS_ERR_BOUNDS);
+                return 0.f;
+            }
+            return __ldg(reinterpret_cast<const float *>(a));
+        };
         static_for<0, KP / 2>([&](auto Ii) {
             constexpr int i = Ii;
             const longlong2 d = d2[i];
-            t[2 * i] = make_float2(__ldg(reinterpret_cast<const float *>(tp[2 * i] + d.x)),
-                                   __ldg(reinterpret_cast<const float *>(tp[2 * i] - d.x)));
+            t[2 * i] = make_float2(ld(tp[2 * i] + d.x), ld(tp[2 * i] - d.x));
             if constexpr (2 * i + 1 < K)
-                t[2 * i + 1] =
-                    make_float2(__ldg(reinterpret_cast<const float *>(tp[2 * i + 1] + d.y)),
-                                __ldg(reinterpret_cast<const float *>(tp[2 * i + 1] - d.y)));
+                t[2 * i + 1] = make_float2(ld(tp[2 * i + 1] + d.y), ld(tp[2 * i + 1] - d.y));
         });
         family_levels<H, K>(t, zz_lo + zl, f, valid, lb, o);
     }

@@ -1,12 +1,15 @@
 """The bounds-checking build of the library (-DHS_CHECK_BOUNDS): every
 shared-memory index of the staged kernel is tested against its own level's
 span in the stage and every global index of its exact pass against its table
-or plane; an index outside would be skipped and reported as HS_ERR_BOUNDS,
-which the binding raises.  The GPU parity tests of the small shapes (every
-level sum, candidate sets, band edges, other shapes, 16-bit storage, signed
-inputs, tile orders) run against that build in a child process and must pass
-unchanged: no index leaves its buffer and the records still equal the FP64
-oracle's.  (compute-sanitizer is not available to these tests.)"""
+or plane; the harmonic-fraction kernels test every shared-memory read against
+its term's box (staged) or every plane read against the plane (gather), and
+each threshold read against the table.  An index outside would be skipped
+and reported as HS_ERR_BOUNDS, which the binding raises.  The GPU parity
+tests of the small shapes (every level sum, candidate sets, band edges, other
+shapes, 16-bit storage, signed inputs, tile orders, the harmonic-fraction
+map) run against that build in a child process and must pass unchanged: no
+index leaves its buffer and the records still equal the FP64 oracle's.
+(compute-sanitizer is not available to these tests.)"""
 import os
 import subprocess
 import sys
