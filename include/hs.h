@@ -156,7 +156,10 @@ HS_API hs_status hs_run(hs_plan *plan, const void *fop, hs_stream_t stream,
  * When fop_f32 is given, every point whose 16-bit level sum could lie on
  * either side of its threshold is re-evaluated from the FP32 copy with the
  * FP32 path's arithmetic, so the candidate set (and each record) equals
- * hs_run on the FP32 plane.  When fop_f32 is NULL the 16-bit sums decide and
+ * hs_run on the FP32 plane: the summing kernel lists the row pairs it marks
+ * in a plan-owned list (one per stream, allocated at the first such run on
+ * it, 4 MiB) and a second kernel decides them from the copy (pairs past the
+ * list's 2^19 are decided in the summing kernel).  When fop_f32 is NULL the 16-bit sums decide and
  * records carry HS_FLAG_LOWP (and HS_FLAG_NEAR inside the error band).
  * For an FP32 plan fop_f32 must be NULL. */
 HS_API hs_status hs_run_checked(hs_plan *plan, const void *fop, const float *fop_f32,

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -36,6 +37,14 @@ struct hs_plan {
     std::vector<float> lmin; // [H]: per level the smallest threshold over all rows
     float *d_ta = nullptr;
     uint32_t *d_order = nullptr;
+    // 16-bit planes with an FP32 copy: the marked row pairs the recheck
+    // kernel decides, one list per stream the plan runs on (runs on
+    // different streams may overlap), allocated at the first such run
+    struct Pending {
+        uint2 *pairs = nullptr;
+        uint32_t *count = nullptr; // [0] pairs listed, [1] recheck blocks done
+    };
+    std::map<cudaStream_t, Pending> pend;
     std::mutex mu;                 // guards the descriptor cache and streams
     const void *map_ptr = nullptr; // plane the cached descriptors encode
     CUtensorMap maps[kMaxStagedH];
@@ -48,6 +57,11 @@ struct hs_plan {
 };
 
 namespace {
+
+// Capacity of a plan's pending list (marked row pairs of a 16-bit plane with
+// an FP32 copy): 2^19 pairs, 4 MiB.  A plane that marks more has the rest
+// decided inside the staged kernel.
+constexpr uint32_t kPendingPairs = 1u << 19;
 
 thread_local std::string g_last_error;
 thread_local int g_last_launches = 0;
@@ -314,7 +328,46 @@ hs_status launch_range(hs_plan *p, const void *fop, const float *fop32, cudaStre
         L.assume_nonneg = p->opt.assume_nonneg != 0;
         L.ring_stages = p->ring_stages;
         L.nt_rt = p->nt;
+        const bool defer = fop32 != nullptr && p->opt.dtype != HS_F32 && p->ring_stages == 0;
+        if (defer) {
+            hs_plan::Pending &pd = p->pend[s];
+            if (!pd.pairs) {
+                // the count and the recheck kernel's done-counter start at
+                // zero; that kernel zeroes both again at the end of each run
+                e = cudaMalloc(&pd.pairs, sizeof(uint2) * kPendingPairs);
+                if (e == cudaSuccess)
+                    e = cudaMalloc(&pd.count, 2 * sizeof(uint32_t));
+                if (e == cudaSuccess)
+                    e = cudaMemset(pd.count, 0, 2 * sizeof(uint32_t));
+                if (e != cudaSuccess) {
+                    cudaFree(pd.pairs);
+                    cudaFree(pd.count);
+                    p->pend.erase(s);
+                    return cuda_fail(e, "pending list");
+                }
+            }
+            L.pend = pd.pairs;
+            L.pend_count = pd.count;
+            L.pend_cap = kPendingPairs;
+        }
         e = launch_staged(L, s);
+        if (e == cudaSuccess && defer) {
+            RecheckLaunch R{};
+            R.pend = L.pend;
+            R.pend_count = L.pend_count;
+            R.pend_cap = kPendingPairs;
+            R.fop32 = fop32;
+            R.n = p->n;
+            R.ld = p->ld;
+            R.nt = p->nt;
+            R.H = p->H;
+            R.ta = p->d_ta;
+            R.rec = c->records;
+            R.counters = c->count;
+            R.cap = c->capacity;
+            e = launch_recheck(R, s);
+            launches = 2;
+        }
         if (e != cudaSuccess)
             return cuda_fail(e, "staged kernel launch");
     } else {
@@ -755,6 +808,10 @@ hs_status hs_plan_destroy(hs_plan *p)
     cudaDeviceSynchronize();
     cudaFree(p->d_ta);
     cudaFree(p->d_order);
+    for (auto &kv : p->pend) {
+        cudaFree(kv.second.pairs);
+        cudaFree(kv.second.count);
+    }
     for (cudaEvent_t ev : p->tev)
         cudaEventDestroy(ev);
     for (cudaEvent_t ev : p->chunk_events)

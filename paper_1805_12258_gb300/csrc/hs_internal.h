@@ -102,7 +102,27 @@ struct StagedLaunch {
     bool assume_nonneg;       // the caller declares the plane non-negative
     int nt_rt;                // the plane's template count (0: sh.nt); a kernel family with
                               // runtime rows serves any odd count up to its compiled one
+    uint2 *pend;              // 16-bit planes with an FP32 copy: device list of marked
+    uint32_t *pend_count;     // row pairs for launch_recheck (null: decided in the
+    uint32_t pend_cap;        // tile); pend_count[0] is zero before the launch and
+                              // launch_recheck zeroes it again
 };
+
+// Decide the pending row pairs of a 16-bit plane's staged launch from its
+// FP32 copy (the FP32 path's level sums, Eq. 2 order) and append the hits.
+struct RecheckLaunch {
+    const uint2 *pend;
+    uint32_t *pend_count;    // [0] pairs listed, [1] blocks done (both zeroed at the end)
+    uint32_t pend_cap;
+    const float *fop32;      // [nt][ld] FP32 copy
+    long long n, ld;
+    int nt, H;
+    const float *ta;         // device thresholds [H][nt]
+    hs_cand *rec;
+    uint32_t *counters;
+    uint32_t cap;
+};
+cudaError_t launch_recheck(const RecheckLaunch &a, cudaStream_t s);
 
 // True when the pipelined kernel is compiled for this shape, groups and stages.
 bool ring_available(const StagedShape &sh, int groups, int stages);

@@ -158,6 +158,9 @@ struct Params {
     int tile_lo;            // first slot of the tile order this launch covers
     int n_slots;            // tiles of this launch
     int nt_rt;              // templates of the plane (<= NT; kernels with runtime rows)
+    uint2 *pend;            // 16-bit planes with an FP32 copy: marked row pairs
+    uint32_t *pend_count;   // (bin, pair) for the recheck kernel, or null
+    uint32_t pend_cap;
 };
 
 // Opt-in bounds checks (-DHS_CHECK_BOUNDS).  A checked build tests every
@@ -197,6 +200,9 @@ struct TileTarget {
     uint32_t cap;
     int zr;                  // runtime-row kernels: the plane's Z = (templates - 1) / 2
     int nt;                  // runtime-row kernels: the plane's template count
+    uint2 *pend;             // pending list of marked row pairs (bin, pair) that the
+    uint32_t *pend_count;    // recheck kernel decides from the FP32 copy; null: the
+    uint32_t pend_cap;       // exact pass decides them in the tile
 };
 
 // Issue the H boxes of the tile starting at bin f0 into the stage (thread 0).
@@ -322,9 +328,10 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
     };
 
     // ---- slow pass (defined here, run below): exact per-level test -----------
-    // scan(z, write, slot): level sums of row z in Eq. 2 order; returns the hit
-    // mask over levels and, when write is set, appends the records from slot.
-    auto scan = [&](int z, bool write, uint32_t rslot) -> uint32_t {
+    // scan(z, write, slot, dry): level sums of row z in Eq. 2 order; returns
+    // the hit mask over levels and, when write is set, appends the records
+    // from slot.  A dry run reads no FP32 copy.
+    auto scan = [&](int z, bool write, uint32_t rslot, bool dry) -> uint32_t {
         float acc = 0.f, ab = 0.f;
         uint32_t hits = 0u;
         float thr[H];
@@ -370,7 +377,7 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
                     nearm |= (fabsf(acc - thr[M]) <= band ? 1u : 0u) << M;
                 }
             });
-            if (need != 0u) {
+            if (need != 0u && !dry) {
                 float w[H];
                 static_for<0, H>([&](auto M) {
                     constexpr int m = M + 1;
@@ -416,15 +423,17 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
         return hits;
     };
 
+    // A dry run of the exact pass on this thread's centre row while the
+    // copies are in flight (the values read are discarded): the pass's code
+    // is then in the instruction cache when a marked pair needs it.  On
+    // 16-bit planes the dry run reads no FP32 copy.
     if constexpr (C::ES == 4) {
-        // FP32: a dry run of the exact pass on this thread's centre row while
-        // the copies are in flight (the values read are discarded): the
-        // pass's code is then in the instruction cache when a marked pair
-        // needs it.  (16-bit planes skip it: their pass may read the FP32
-        // copy, which a dry run has no business touching.)
         float pw[H];
         const uint32_t dry = scan32(0, pw);
         asm volatile("" ::"r"(dry), "f"(pw[H - 1]));
+    } else if (tt.pend == nullptr) {
+        const uint32_t dry = scan(0, false, 0u, true);
+        asm volatile("" ::"r"(dry));
     }
 
     // CTA-uniform outcome of the bounded wait for the stage
@@ -599,16 +608,29 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
                     put_record(tt.rec, rsl++, tt.cap, (uint32_t)f, -zz, M + 1, 0u, pb[M]);
             });
         } else {
+            if (tt.pend != nullptr) {
+                // deferred: the marked pair goes to the pending list and the
+                // recheck kernel decides both rows from the FP32 copy (all
+                // pairs' reads in flight together, after this grid); only a
+                // pair the full list cannot take is decided here
+                const uint32_t ps = warp_reserve(tt.pend_count, zz >= 0 ? 1u : 0u);
+                if (zz >= 0 && ps < tt.pend_cap) {
+                    tt.pend[ps] = make_uint2((uint32_t)f, (uint32_t)zz);
+                    zz = -1;
+                }
+                if (!__any_sync(0xffffffffu, zz >= 0))
+                    continue;
+            }
             if (zz >= 0) {
-                ht = scan(zz, false, 0u);
+                ht = scan(zz, false, 0u, false);
                 if (zz > 0)
-                    hb = scan(-zz, false, 0u);
+                    hb = scan(-zz, false, 0u, false);
             }
             uint32_t rsl = warp_reserve(tt.counters, (uint32_t)(__popc(ht) + __popc(hb)));
             if (ht)
-                scan(zz, true, rsl);
+                scan(zz, true, rsl, false);
             if (hb)
-                scan(-zz, true, rsl + (uint32_t)__popc(ht));
+                scan(-zz, true, rsl + (uint32_t)__popc(ht), false);
         }
     }
     return true;
@@ -646,8 +668,10 @@ __global__ void __launch_bounds__(TB, (resident_ctas<NT, H, TB, T>()))
         }
     }
     __syncthreads();
-    const TileTarget tt{p.maps,     p.split1, p.fop32, p.n,       p.ld,
-                        p.rec,      p.counters, p.cap, (p.nt_rt - 1) / 2, p.nt_rt};
+    const TileTarget tt{p.maps,     p.split1,   p.fop32, p.n,
+                        p.ld,       p.rec,      p.counters, p.cap,
+                        (p.nt_rt - 1) / 2, p.nt_rt, p.pend,  p.pend_count,
+                        p.pend_cap};
     uint32_t parity = 0;
     for (int i = (int)blockIdx.x; i < p.n_slots; i += (int)gridDim.x, parity ^= 1u) {
         const int slot = p.tile_lo + i;
@@ -996,6 +1020,13 @@ cudaError_t launch_one(const StagedLaunch &a, cudaStream_t s)
     p.tile_lo = a.tile_lo;
     p.n_slots = a.tile_hi - a.tile_lo;
     p.nt_rt = a.nt_rt > 0 ? a.nt_rt : NT;
+    if constexpr (sizeof(T) == 2) {
+        if (a.fop32 != nullptr) {
+            p.pend = a.pend;
+            p.pend_count = a.pend_count;
+            p.pend_cap = a.pend_cap;
+        }
+    }
     if (p.n_slots <= 0)
         return cudaSuccess;
     if (p.nt_rt > NT || p.nt_rt % 2 == 0 || (!RT && p.nt_rt != NT))

@@ -174,6 +174,54 @@ def test_hfrac_kernels_orders_and_ranges_agree():
     assert_matches_oracle(results[0], ref, near)
 
 
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+def test_lowp_recheck_past_the_pending_list(dtype):
+    # A 16-bit plane with its FP32 copy: the summing kernel lists marked row
+    # pairs for the recheck kernel, 2^19 at most; with thresholds below every
+    # value all 43 x 13,000 = 559,000 pairs are marked, so the last ones are
+    # decided inside the summing kernel.  Every level sum of every point is
+    # a record either way, equal to the oracle's on the FP32 plane.
+    nt, n, H = 85, 13000, 16
+    plane = synth.noise(nt, n, seed=91)
+    low = _bf16_bits(plane) if dtype == "bf16" else plane.astype(np.float16)
+    ta = np.full((H, nt), -1e30, np.float32)
+    recs, cnt, st, used = run_gpu(low, H, ta, cap=nt * n * H, dtype=dtype, fop32=plane,
+                                  assume_nonneg=True)
+    assert used == "staged" and st == hs.HS_OK and cnt == nt * n * H
+    Z = (nt - 1) // 2
+    got = np.full((H, nt, n), np.nan)
+    got[recs["k"].astype(int) - 1, recs["z"].astype(int) + Z, recs["bin"].astype(int)] = \
+        recs["power"]
+    np.testing.assert_allclose(got, oracle.planes(plane, H), rtol=RTOL, atol=0)
+    assert not (recs["flags"] != 0).any()
+
+
+def test_lowp_recheck_on_two_streams_of_one_plan():
+    # each stream has its own pending list: two 16-bit planes run on one plan
+    # from two streams, repeatedly, each giving the FP32 path's records
+    nt, n, H = 85, 20000, 16
+    planes = [synth.noise(nt, n, seed=s) for s in (101, 102)]
+    for i, p_ in enumerate(planes):
+        wl = synth.Workload("t", nt, n, H, 7 + i, 1e-4, 20, (200, 1200), (-2, 2))
+        synth.inject(p_, synth.draw_signals(wl))
+    ta = synth.thresholds(1e-4, H, nt)
+    refs = [run_gpu(p_, H, ta)[0] for p_ in planes]
+    lows = [torch.from_numpy(_bf16_bits(p_).view(np.int16)).cuda().view(torch.bfloat16)
+            for p_ in planes]
+    f32s = [torch.from_numpy(p_).cuda() for p_ in planes]
+    streams = [torch.cuda.Stream() for _ in planes]
+    bufs = [hs.CandBuffer(1 << 20) for _ in planes]
+    with hs.Plan(nt, n, H, ta, dtype="bf16", assume_nonneg=True) as plan:
+        for _ in range(5):
+            for i in range(2):
+                plan.run(lows[i], bufs[i], streams[i], fop_f32=f32s[i])
+        torch.cuda.synchronize()
+        for i in range(2):
+            recs, cnt, st = bufs[i].fetch(streams[i])
+            assert st == hs.HS_OK and cnt == len(refs[i]) > 0
+            assert np.array_equal(recs, refs[i])
+
+
 @pytest.mark.parametrize("nt,n,H,dtype", [(85, 20000, 16, "f32"), (21, 50000, 8, "f32"),
                                           (85, 8192, 16, "bf16")])
 def test_declared_nonnegative_planes_same_records(nt, n, H, dtype):
