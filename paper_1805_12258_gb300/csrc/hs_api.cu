@@ -296,7 +296,8 @@ hs_status launch_range(hs_plan *p, const void *fop, const float *fop32, cudaStre
         L.cap = c->capacity;
         L.f_lo = f_lo;
         L.f_hi = f_hi;
-        L.order = full ? p->d_order : nullptr;
+        // the table only for a non-linear order (its default is linear)
+        L.order = full && p->opt.order > 1 ? p->d_order : nullptr;
         launches = 0;
         e = launch_hfrac_staged(L, s, &launches);
         if (e != cudaSuccess)

@@ -136,6 +136,31 @@ def test_hfrac_staged_every_level_sum(nt, n, H, tb):
     np.testing.assert_allclose(got, ref, rtol=RTOL, atol=0)
 
 
+@pytest.mark.parametrize("nt,n,H", [(3, 200004, 16), (3, 200004, 8), (1, 300004, 16)])
+def test_hfrac_large_plane_every_level_sum(nt, n, H):
+    # thousands of tiles, the last one ragged
+    plane = synth.noise(nt, n, seed=nt * 13 + n + H)
+    got, used = _all_sums(plane, H, index="hfrac")
+    assert used == "staged"
+    ref = oracle.planes(plane, H, index=oracle.HFRAC)
+    np.testing.assert_allclose(got, ref, rtol=RTOL, atol=0)
+
+
+def test_hfrac_candidates_equal_oracle_and_gather():
+    nt, n, H = 85, 200004, 16
+    plane = synth.noise(nt, n, seed=77)
+    wl = synth.Workload("t", nt, n, H, 5, 1e-4, 12, (2000, 12000), (-2, 2))
+    synth.inject(plane, synth.draw_signals(wl))
+    ta = synth.thresholds(1e-5, H, nt)
+    recs, cnt, st, used = run_gpu(plane, H, ta, index="hfrac")
+    assert used == "staged" and st == hs.HS_OK and cnt > 0
+    ref, near = oracle.detect(plane, H, ta, index=oracle.HFRAC, threads=16)
+    assert_matches_oracle(recs, ref, near)
+    g, _, st2, _ = run_gpu(plane, H, ta, index="hfrac", kernel="generic")
+    assert st2 == hs.HS_OK and np.array_equal(np.sort(g, order=["k", "z", "bin"]),
+                                               np.sort(recs, order=["k", "z", "bin"]))
+
+
 @pytest.mark.parametrize("nt,n,H", [(85, 1000, 16), (21, 777, 8), (127, 333, 16), (1, 50, 8)])
 def test_hfrac_gather_every_level_sum(nt, n, H):
     # the gather pair kernel: forced, or for rows that are not 16-byte multiples
