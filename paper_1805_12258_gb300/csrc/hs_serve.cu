@@ -50,6 +50,41 @@ __host__ __device__ inline void philox4x32_10(uint32_t c[4], uint32_t k0, uint32
     }
 }
 
+// The ten round keys of a key (k0, k1): the same for every counter, so the
+// noise kernel takes them as launch parameters instead of bumping the key
+// in each thread.
+struct RoundKeys {
+    uint32_t k0[10], k1[10];
+};
+
+RoundKeys round_keys(uint32_t k0, uint32_t k1)
+{
+    RoundKeys r;
+    for (int i = 0; i < 10; ++i) {
+        r.k0[i] = k0;
+        r.k1[i] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return r;
+}
+
+// philox4x32_10 with the round keys given.
+__device__ __forceinline__ void philox4x32_10_rk(uint32_t c[4], const RoundKeys &rk)
+{
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c[1] ^ rk.k0[i];
+        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c[3] ^ rk.k1[i];
+        c[1] = (uint32_t)p1;
+        c[3] = (uint32_t)p0;
+        c[0] = n0;
+        c[2] = n2;
+    }
+}
+
 constexpr uint32_t kNoiseTag = 0x6E6F6973u;  // counter word 3 of the noise stream
 constexpr uint32_t kSignalTag = 0x7369676Eu; // counter word 3 of the signal draws
 constexpr int kMaxSignals = 16;
@@ -66,17 +101,25 @@ __device__ __forceinline__ float exp1(uint32_t r)
     return fmaxf(0.0f - __logf(u), 0.0f);
 }
 
-// Noise plane, one Philox call per 4 consecutive bins of a row (grid.y = row).
+// Noise plane, one Philox call per 4 consecutive bins of a row (grid.y =
+// row).  A thread makes kQuadsPerThread quads, blockDim.x quads apart, so each
+// store instruction of a warp writes contiguous bytes.
+constexpr int kQuadsPerThread = 4;
+
 template <bool LOWP>
 __global__ void synth_noise(float *__restrict__ f32, __nv_bfloat16 *__restrict__ bf, long long n,
-                            long long ld, long long width, uint32_t k0, uint32_t k1)
+                            long long ld, long long width, const __grid_constant__ RoundKeys rk)
 {
     const int row = (int)blockIdx.y;
     const long long quads = width / 4; // bins [0, width) of the row are written
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < quads;
-         q += (long long)gridDim.x * blockDim.x) {
+    const long long q0 = (long long)blockIdx.x * blockDim.x * kQuadsPerThread + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < kQuadsPerThread; ++k) {
+        const long long q = q0 + (long long)k * blockDim.x;
+        if (q >= quads)
+            break;
         uint32_t c[4] = {(uint32_t)q, (uint32_t)(q >> 32), (uint32_t)row, kNoiseTag};
-        philox4x32_10(c, k0, k1);
+        philox4x32_10_rk(c, rk);
         const long long f = q * 4;
         float4 v;
         v.x = f + 0 < n ? exp1(c[0]) : 0.f;
@@ -188,12 +231,16 @@ hs_status synth(void *fop, float *fop32, int dtype, int nt, long long n, long lo
     const long long width = write_pad ? ld : (n + 3) / 4 * 4;
     const long long quads = width / 4;
     const int tpb = 256;
-    const unsigned gx = (unsigned)std::min<long long>((quads + tpb - 1) / tpb, 1 << 16);
-    const dim3 grid(gx, (unsigned)nt);
+    const long long per_block = (long long)tpb * kQuadsPerThread;
+    const long long gx = (quads + per_block - 1) / per_block;
+    if (gx > 0x7fffffffLL)
+        return fail(HS_ERR_INVALID, "hs_synth_fop: row too long");
+    const dim3 grid((unsigned)gx, (unsigned)nt);
+    const RoundKeys rk = round_keys(k0, k1);
     if (bf)
-        synth_noise<true><<<grid, tpb, 0, s>>>(f32, bf, n, ld, width, k0, k1);
+        synth_noise<true><<<grid, tpb, 0, s>>>(f32, bf, n, ld, width, rk);
     else
-        synth_noise<false><<<grid, tpb, 0, s>>>(f32, bf, n, ld, width, k0, k1);
+        synth_noise<false><<<grid, tpb, 0, s>>>(f32, bf, n, ld, width, rk);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && n_signals > 0) {
         synth_signals<<<1, 1, 0, s>>>(f32, bf, nt, n, ld, draw_signals(seed, n, n_signals));
