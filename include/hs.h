@@ -160,8 +160,10 @@ HS_API hs_status hs_run(hs_plan *plan, const void *fop, hs_stream_t stream,
  * in a plan-owned list (one per stream, allocated at the first such run on
  * it, 4 MiB) and a second kernel decides them from the copy (pairs past the
  * list's 2^19 are decided in the summing kernel).  When fop_f32 is NULL the 16-bit sums decide and
- * records carry HS_FLAG_LOWP (and HS_FLAG_NEAR inside the error band).
- * For an FP32 plan fop_f32 must be NULL. */
+ * records carry HS_FLAG_LOWP (and HS_FLAG_NEAR inside the error band).  An
+ * FP16 value above 65504 is stored as +inf: with the copy its pairs are
+ * decided from the copy; without it their records carry power +inf and both
+ * flags.  For an FP32 plan fop_f32 must be NULL. */
 HS_API hs_status hs_run_checked(hs_plan *plan, const void *fop, const float *fop_f32,
                          hs_stream_t stream, const hs_cand_buf *cands);
 

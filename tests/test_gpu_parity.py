@@ -221,6 +221,34 @@ def test_lowp_recheck_past_the_pending_list(dtype):
     assert not (recs["flags"] != 0).any()
 
 
+def test_f16_overflow_is_decided_by_the_fp32_copy():
+    # Values above 65,504 are stored as +inf in FP16.  The prefilter marks
+    # their pairs and the FP32 copy decides them, so the records equal the
+    # FP32 path's; without the copy they are records with power +inf,
+    # flagged as decided in 16 bits and near their threshold.
+    nt, n, H = 85, 20000, 16
+    plane = synth.noise(nt, n, seed=41)
+    hot = [(42, 5000), (10, 12345), (84, 19999), (0, 0)]
+    for r, f in hot:
+        plane[r, f] = 1.0e5
+    ta = synth.thresholds(1e-4, H, nt)
+    with np.errstate(over="ignore"):
+        low = plane.astype(np.float16)
+    assert np.isinf(low[42, 5000])
+    ref, nref, _, _ = run_gpu(plane, H, ta, assume_nonneg=True)
+    got, ngot, st, used = run_gpu(low, H, ta, dtype="f16", fop32=plane, assume_nonneg=True)
+    assert used == "staged" and st == hs.HS_OK and ngot == nref
+    assert np.array_equal(got, ref)
+    bare, _, st2, _ = run_gpu(low, H, ta, dtype="f16", assume_nonneg=True)
+    assert st2 == hs.HS_OK
+    at_inf = bare[np.isinf(bare["power"])]
+    assert len(at_inf) > 0
+    assert ((at_inf["flags"] & hs.HS_FLAG_LOWP) != 0).all()
+    assert ((at_inf["flags"] & hs.HS_FLAG_NEAR) != 0).all()
+    assert {(int(r - 42), int(f)) for r, f in hot} <= \
+        {(int(x["z"]), int(x["bin"])) for x in at_inf if x["k"] == 1}
+
+
 def test_lowp_recheck_on_two_streams_of_one_plan():
     # each stream has its own pending list: two 16-bit planes run on one plan
     # from two streams, repeatedly, each giving the FP32 path's records
