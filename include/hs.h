@@ -73,18 +73,24 @@ typedef struct {
     int dtype;      /* hs_dtype of the stored plane (default HS_F32) */
     int index;      /* hs_index (default HS_INDEX_STRETCH, Eq. 1-2) */
     int zround;     /* hs_zround (default HS_ZROUND_SYMMETRIC) */
-    int kernel;     /* hs_kernel: AUTO picks the staged kernel when it applies */
-    int tile_bins;  /* bins per CTA of the staged kernel: 0 = default */
-    int order;      /* tile order: 0 = default (semitone), 1 = linear, 2 = octave (mantissa of
-                       the tile index), 3 = semitone (fractional part of 12 log2 of the
-                       tile index) */
+    int kernel;     /* hs_kernel: AUTO picks the staged kernel when it applies -- the
+                       stretch map: a compiled shape family, symmetric rounding, rows a
+                       multiple of 16 bytes; HS_INDEX_HFRAC: FP32, symmetric rounding,
+                       H = 8 or 16, rows a multiple of 16 bytes (one launch per level
+                       family).  Otherwise (or GENERIC) the generic kernel; for HFRAC at
+                       H = 8 or 16 with symmetric rounding, its gather form. */
+    int tile_bins;  /* bins per CTA of the staged kernel: 0 = default (128; 64 for
+                       HS_INDEX_HFRAC, which takes 64 or 128) */
+    int order;      /* tile order: 0 = default (semitone; linear for HS_INDEX_HFRAC),
+                       1 = linear, 2 = octave (mantissa of the tile index), 3 = semitone
+                       (fractional part of 12 log2 of the tile index) */
     int grid_per_sm;/* staged kernel: 0 = one CTA per tile; k > 0 = k resident CTAs per SM
                        that walk the tiles */
     int row_pitch;  /* elements between plane rows (0 = n_bins); >= n_bins.  The staged
                        kernel needs row_pitch * element size to be a multiple of 16 bytes */
     int stages;     /* staged kernel: 0 = one CTA per tile (or grid_per_sm); s > 0 = one
                        persistent CTA per SM with an s-stage ring of tiles, filled by a
-                       producer warp while consumer groups sum */
+                       producer warp while consumer groups sum (stretch map only) */
     int z_split;    /* with stages > 0: consumer groups of tile_bins threads (0 = 2) */
     int assume_nonneg; /* 1: the caller declares every plane value non-negative and not
                        NaN (detected power is); the staged kernel then skips its per-value
@@ -129,8 +135,8 @@ typedef struct hs_plan hs_plan;
  *                finite); copied, the caller keeps ownership.
  *  opt         : NULL for defaults.
  * Allocates the plan's device tables on the current device.
- * Errors: HS_ERR_INVALID, HS_ERR_UNSUPPORTED (HFRAC with H > 32),
- *         HS_ERR_OOM, HS_ERR_CUDA. */
+ * Errors: HS_ERR_INVALID, HS_ERR_UNSUPPORTED (kernel = STAGED, or stages > 0,
+ *         where no such kernel applies), HS_ERR_OOM, HS_ERR_CUDA. */
 HS_API hs_status hs_plan_create(hs_plan **out, int n_templates, int64_t n_bins, int H,
                          const float *thresholds, const hs_options *opt);
 
