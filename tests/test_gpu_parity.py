@@ -161,6 +161,29 @@ def test_hfrac_candidates_equal_oracle_and_gather():
                                                np.sort(recs, order=["k", "z", "bin"]))
 
 
+def test_hfrac_padded_rows_never_read_the_pad():
+    # a ragged plane in padded rows runs the staged kernel (its boxes end at
+    # the last bin, so the pad -- NaN here -- is never read) and gives the
+    # gather kernel's records on the unpadded plane, which are the oracle's
+    nt, n, H = 85, 30011, 16
+    plane = synth.noise(nt, n, seed=43)
+    ta = synth.thresholds(1e-4, H, nt)
+    ld = n + 5  # 30016: rows a multiple of 16 bytes
+    padded = np.full((nt, ld), np.nan, np.float32)
+    padded[:, :n] = plane
+    dev = torch.from_numpy(padded).cuda()
+    cands = hs.CandBuffer(1 << 20)
+    with hs.Plan(nt, n, H, ta, index="hfrac", row_pitch=ld) as plan:
+        assert plan.kernel == "staged"
+        plan.run(dev, cands)
+        got, cnt, st = cands.fetch()
+    assert st == hs.HS_OK and cnt > 0 and not np.isnan(got["power"]).any()
+    ref, nref, _, used = run_gpu(plane, H, ta, index="hfrac")
+    assert used == "generic" and np.array_equal(got, ref)
+    o, near = oracle.detect(plane, H, ta, index=oracle.HFRAC, threads=8)
+    assert_matches_oracle(got, o, near)
+
+
 @pytest.mark.parametrize("nt,n,H", [(85, 1000, 16), (21, 777, 8), (127, 333, 16), (1, 50, 8)])
 def test_hfrac_gather_every_level_sum(nt, n, H):
     # the gather pair kernel: forced, or for rows that are not 16-byte multiples
