@@ -604,17 +604,21 @@ def test_a_wait_that_runs_out_reports_timeout_and_the_context_stays_usable():
     assert_matches_oracle(recs, ref, near)
 
 
-@pytest.mark.parametrize("kernel", ["staged", "generic"])
-def test_run_host_matches_run(kernel):
+@pytest.mark.parametrize("kernel,index", [("staged", "stretch"), ("generic", "stretch"),
+                                          ("staged", "hfrac"), ("generic", "hfrac")])
+def test_run_host_matches_run(kernel, index):
+    # end to end from pinned host memory (the plane copied in chunks while
+    # earlier chunks are summed) gives the device run's records
     wl = synth.small_plane(seed=2)
     plane = synth.make_plane(wl)
     ta = synth.thresholds(1e-4, wl.H, wl.n_templates)
-    ref, n_ref, _, _ = run_gpu(plane, wl.H, ta, kernel=kernel)
+    ref, n_ref, _, used = run_gpu(plane, wl.H, ta, kernel=kernel, index=index)
+    assert used == kernel and n_ref > 0
     host = torch.from_numpy(plane).pin_memory()
     dev = torch.empty_like(host, device="cuda")
     cands = hs.CandBuffer(1 << 16)
     out = np.zeros(1 << 16, hs.CAND_DTYPE)
-    with hs.Plan(wl.n_templates, wl.n_bins, wl.H, ta, kernel=kernel) as plan:
+    with hs.Plan(wl.n_templates, wl.n_bins, wl.H, ta, kernel=kernel, index=index) as plan:
         st, n = plan.run_host(host, dev, cands, out)
     assert st == hs.HS_OK and n == n_ref
     assert np.array_equal(hs.sort_records(out[:n]), ref)
