@@ -353,6 +353,21 @@ def test_signed_inputs_take_the_exact_path():
     assert_matches_oracle(recs, ref, near, rtol=1e-5)
 
 
+def test_signed_lowp_with_copy_equals_the_fp32_path():
+    # A signed 16-bit plane: every row of a thread that loads a negative
+    # value is marked and goes to the recheck kernel, which decides it from
+    # the FP32 copy -- the FP32 path's records (which the oracle confirms)
+    plane = synth.random_plane(21, 4096, seed=5, lo=-1.0, hi=1.0)
+    plane[:, ::7] = np.abs(plane[:, ::7]) * 6.0
+    ta = np.tile(np.array([[0.9 + 0.3 * k] for k in range(8)], np.float32), (1, 21))
+    ref, nref, _, used32 = run_gpu(plane, 8, ta)
+    got, n, st, used = run_gpu(_bf16_bits(plane), 8, ta, dtype="bf16", fop32=plane)
+    assert used32 == used == "staged" and st == hs.HS_OK and n == nref > 0
+    assert np.array_equal(got, ref)
+    o, near = oracle.detect(plane, 8, ta)
+    assert_matches_oracle(got, o, near, rtol=1e-5)
+
+
 def test_per_row_thresholds():
     plane = synth.noise(85, 4096, seed=21)
     rng = np.random.default_rng(4)
