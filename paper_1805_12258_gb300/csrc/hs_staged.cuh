@@ -566,7 +566,8 @@ __device__ __forceinline__ bool sum_tile(const P &p, const TileTarget &tt,
         constexpr int n0 = Z + 1 < 32 ? Z + 1 : 32;
         mask = (uint64_t)(__brev(~clear[0]) >> (32 - n0));
         if constexpr (Z >= 32)
-            mask |= (uint64_t)((__brev(~clear[1]) >> (63 - Z)) & ((1u << (Z - 31)) - 1u)) << 32;
+            mask |= (uint64_t)((__brev(~clear[1]) >> (63 - Z)) &
+                               (uint32_t)((1ull << (Z - 31)) - 1ull)) << 32;
         if constexpr (BANDED)
             out_ok = !any_of(!out_ok); // CTA-uniform, like ok
     }
