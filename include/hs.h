@@ -164,8 +164,9 @@ HS_API hs_status hs_run(hs_plan *plan, const void *fop, hs_stream_t stream,
  * FP32 path's arithmetic, so the candidate set (and each record) equals
  * hs_run on the FP32 plane: the summing kernel lists the row pairs it marks
  * in a plan-owned list (one per stream, allocated at the first such run on
- * it, 4 MiB) and a second kernel decides them from the copy (pairs past the
- * list's 2^19 are decided in the summing kernel).  When fop_f32 is NULL the 16-bit sums decide and
+ * it, 4 MiB -- make that first run outside stream capture) and a second
+ * kernel decides them from the copy (pairs past the list's 2^19 are decided
+ * in the summing kernel).  When fop_f32 is NULL the 16-bit sums decide and
  * records carry HS_FLAG_LOWP (and HS_FLAG_NEAR inside the error band).  An
  * FP16 value above 65504 is stored as +inf: with the copy its pairs are
  * decided from the copy; without it their records carry power +inf and both
