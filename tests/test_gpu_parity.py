@@ -639,6 +639,37 @@ def test_run_host_matches_run(kernel, index):
     assert np.array_equal(hs.sort_records(out[:n]), ref)
 
 
+@pytest.mark.parametrize("kind", ["f32", "bf16", "hfrac"])
+def test_plan_run_replays_in_a_cuda_graph(kind):
+    # after one run on a stream (the pending list, descriptors and kernel
+    # attributes exist then), a run captured on that stream replays with the
+    # same records: the FP32 staged kernel, the 16-bit one with its recheck
+    # kernel (a programmatic dependent launch), the harmonic-fraction families
+    nt, n, H = 85, 20000, 16
+    plane = synth.noise(nt, n, seed=61)
+    wl = synth.Workload("t", nt, n, H, 9, 1e-4, 12, (500, 2500), (-2, 2))
+    synth.inject(plane, synth.draw_signals(wl))
+    ta = synth.thresholds(1e-4, H, nt)
+    f32 = torch.from_numpy(plane).cuda()
+    kw = {"hfrac": dict(index="hfrac"), "bf16": dict(dtype="bf16")}.get(kind, {})
+    fop = f32.to(torch.bfloat16) if kind == "bf16" else f32
+    copy = f32 if kind == "bf16" else None
+    cands = hs.CandBuffer(1 << 18)
+    s = torch.cuda.Stream()
+    with hs.Plan(nt, n, H, ta, assume_nonneg=True, **kw) as plan:
+        plan.run(fop, cands, s, fop_f32=copy)
+        ref, nref, st = cands.fetch(s)
+        assert st == hs.HS_OK and nref > 0
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            plan.run(fop, cands, s, fop_f32=copy)
+        for _ in range(3):
+            g.replay()  # on torch's current stream
+            torch.cuda.synchronize()
+            got, cnt, st = cands.fetch(s)
+            assert st == hs.HS_OK and cnt == nref and np.array_equal(got, ref)
+
+
 def test_launch_count_is_one():
     plane = synth.noise(21, 4096, seed=12)
     run_gpu(plane, 8, synth.thresholds(1e-3, 8, 21))
