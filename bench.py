@@ -313,8 +313,9 @@ def run_reference(args):
 def precision_summary(fop32, ta, H, ref_records, nonneg, steps=500):
     """The plane stored as BF16 and as FP16 (rounded on the device), summed
     with FP32 accumulation, levels near a threshold re-decided from the FP32
-    copy; per storage: mean kernel time (plan events), throughput, roofline
-    on its own bytes, and whether its records equal the FP32 path's."""
+    copy; per storage: mean time per run (runs back to back, CUDA events
+    around them), throughput, roofline on its own bytes, and whether its
+    records equal the FP32 path's."""
     import torch
 
     from paper_1805_12258_gb300 import hs
@@ -332,16 +333,16 @@ def precision_summary(fop32, ta, H, ref_records, nonneg, steps=500):
             clocks = ClockSampler(torch.cuda.current_device())
             clocks.start()
             time.sleep(0.3)
-            plan.set_timing(True)
-            plan.kernel_time()
-            for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(steps):  # back to back (summing and recheck kernels)
                 plan.run(low, c, stream, fop_f32=fop32)
+            e1.record(stream)
             torch.cuda.synchronize()
             clk = clocks.stop()
-            ms, k = plan.kernel_time()
-            plan.set_timing(False)
             recs, cnt, st = c.fetch(stream)
-        us = ms / max(k, 1) * 1e3
+        us = e0.elapsed_time(e1) / steps * 1e3
         algo = nt * n * 2 + H * nt * 4 + 16 * int(cnt) + 8
         out[dt] = {"storage": dt, "recheck": "FP32 copy", "mean_kernel_us": us,
                    "points_per_s": nt * n / (us / 1e6), "candidates": int(cnt),
@@ -359,9 +360,10 @@ def precision_summary(fop32, ta, H, ref_records, nonneg, steps=500):
 
 def hfrac_summary(fop32, ta, H, stretch_us, steps=20):
     """The harmonic-fraction index map (level k sums the terms h/k, h = 1..k)
-    on the same plane: its staged kernels' mean time per run (plan events,
-    one launch per level family), throughput, the ratio to the stretch map's
-    kernel time, and its records (returned beside the summary)."""
+    on the same plane: its staged kernels' mean time per run (runs back to
+    back, CUDA events around them; one launch per level family), throughput,
+    the ratio to the stretch map's kernel time, and its records (returned
+    beside the summary)."""
     import torch
 
     from paper_1805_12258_gb300 import hs
@@ -376,18 +378,18 @@ def hfrac_summary(fop32, ta, H, stretch_us, steps=20):
         clocks = ClockSampler(torch.cuda.current_device())
         clocks.start()
         time.sleep(0.3)
-        plan.set_timing(True)
-        plan.kernel_time()
-        for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):  # back to back
             plan.run(fop32, c, stream)
+        e1.record(stream)
         launches = hs.hs_last_launch_count()
         torch.cuda.synchronize()
         clk = clocks.stop()
-        ms, k = plan.kernel_time()
-        plan.set_timing(False)
         recs, cnt, st = c.fetch(stream)
         kernel, tb = plan.kernel, plan.tile_bins
-    us = ms / max(k, 1) * 1e3
+    us = e0.elapsed_time(e1) / steps * 1e3
     algo = nt * n * 4 + H * nt * 4 + 16 * int(cnt) + 8
     return {"index": "hfrac", "kernel": kernel, "tile_bins": tb, "launches_per_run": launches,
             "mean_us_per_run": us, "points_per_s": nt * n / (us / 1e6),
@@ -454,14 +456,17 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     clocks = ClockSampler(local)
-    plan.set_timing(True)
+    # a plane smaller than L2 is timed cold: 512 MB of scratch is written
+    # before every launch and the throughput comes from the launches' own
+    # CUDA-event times (the scratch writes stay outside them).  Otherwise the
+    # launches run back to back with no event between them (a pair of events
+    # per launch costs about 4 us of a 146 us step), and the average launch
+    # duration is the timed region's elapsed time over the steps.
+    cold = nt * n * es < L2_BYTES
+    plan.set_timing(cold)
     plan.kernel_time()  # clear
     clocks.start()
     time.sleep(0.3)  # sampler warm-up
-    # a plane smaller than L2 is timed cold: 512 MB of scratch is written
-    # before every launch and the throughput comes from the launches' own
-    # CUDA-event times (the scratch writes stay outside them)
-    cold = nt * n * es < L2_BYTES
     scratch = torch.empty(512 << 20, dtype=torch.uint8, device="cuda") if cold else None
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches_before = 0
@@ -482,8 +487,17 @@ def run_ours(args):
         dist.barrier()
     clk = clocks.stop()
     elapsed_ms = e0.elapsed_time(e1)
-    kern_ms, kern_n = plan.kernel_time()
+    kern_ms, kern_n = plan.kernel_time() if cold else (elapsed_ms, args.steps)
+    plan.set_timing(True)
     hot_us = None
+    per_launch_event_us = None
+    if not cold:  # for reference: the same launches, each inside its own event pair
+        plan.kernel_time()
+        for _ in range(min(args.steps, 200)):
+            step()
+        torch.cuda.synchronize()
+        pk, pn = plan.kernel_time()
+        per_launch_event_us = pk / max(pn, 1) * 1e3
     if cold:  # the same launches back to back, plane resident in L2
         plan.kernel_time()
         for _ in range(args.steps):
@@ -634,6 +648,10 @@ def run_ours(args):
                          "peak_kind": f"{peak_kind} copy bandwidth",
                          "kernel": kname, "algo_bytes_per_launch": algo_bytes,
                          "mean_kernel_us": mean_kernel_s * 1e6,
+                         "duration_from": ("each launch's own event pair" if cold else
+                                           "timed region elapsed / steps (launches back "
+                                           "to back, counter reset included)"),
+                         "per_launch_event_us": per_launch_event_us,
                          "frac_of_8tbs": algo_bytes / mean_kernel_s / 8e12},
             "precision": precision if precision is not None else sections.get("precision"),
             "batch": sections.get("batch"),
