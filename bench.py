@@ -12,8 +12,9 @@ value      : points harmonic-summed per second (85 * 2^21 points per plane per
 e2e        : the same metric through hs_run_host with the plane in pinned host
              memory: host->device copy, summing, candidate read-back per step.
 roofline   : the staged kernel's algorithmic bytes per launch (plane once +
-             thresholds + candidate records) / its mean event-timed duration,
-             against the measured HBM copy bandwidth.
+             thresholds + candidate records) / its average launch duration
+             (the timed region's CUDA-event time over its steps, launched
+             back to back), against the measured HBM copy bandwidth.
 cpu_baseline: the FP64 oracle on a bounded sample of the same plane, all host
              cores (threads over bin ranges).
 --impl reference: the oracle alone, timed on the host cores (rank 0 only).
@@ -26,7 +27,10 @@ precision  the same plane stored as BF16 and as FP16 (FP32 recheck copy):
 batch      64 beams log-uniform in [2^18, 2^22] bins packed in one plane, one
            summing launch per graph replay, against back-to-back hs_runs;
 serve      the serving engine for 2 s of Poisson arrivals at 1000 beams/s:
-           p50/p99 latency, then closed-loop capacity.
+           p50/p99 latency, then closed-loop capacity;
+hfrac      the harmonic-fraction index map on the same plane: time per run,
+           ratio to the stretch map, records in an oracle window (the oracle
+           run in the CPU-baseline leg).
 """
 from __future__ import annotations
 
