@@ -70,6 +70,24 @@ def test_plan_create_rejects_bad_options(L):
                             ctypes.byref(opt)) == hs.HS_ERR_INVALID
 
 
+@pytest.mark.parametrize("H,opts,why", [
+    (13, dict(index=1, kernel=2), "harmonic-fraction"),              # H not compiled
+    (16, dict(index=1, kernel=2, tile_bins=96), "harmonic-fraction"),  # tile width
+    (16, dict(index=1, kernel=2, zround=1), "harmonic-fraction"),      # floor rounding
+    (16, dict(index=1, kernel=2, row_pitch=1001), "harmonic-fraction"),  # rows not 16 B
+    (16, dict(index=1, stages=3), "pipelined")])
+def test_plan_create_refuses_missing_harmonic_fraction_kernels(L, H, opts, why):
+    # the kernel choice is made before any device allocation: a staged
+    # harmonic-fraction kernel is asked for where none is compiled
+    ta = np.ones((H, 85), np.float32)
+    opt = hs.hs_options(**opts)
+    out = ctypes.c_void_p()
+    st = L.hs_plan_create(ctypes.byref(out), 85, 1000, H, ta.ctypes.data, ctypes.byref(opt))
+    assert st == hs.HS_ERR_UNSUPPORTED
+    assert why in L.hs_last_error().decode()
+    assert out.value is None
+
+
 def test_run_rejects_null_plan_and_pointers(L):
     buf = hs.hs_cand_buf(None, None, 0)
     assert L.hs_run(None, None, None, ctypes.byref(buf)) == hs.HS_ERR_INVALID
