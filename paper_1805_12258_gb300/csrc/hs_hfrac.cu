@@ -26,7 +26,6 @@
 // row offsets floor(zz h/K) * ld kept in a shared table.
 #include <algorithm>
 #include <cstring>
-#include <mutex>
 #include <vector>
 
 #include "hs_device.cuh"
@@ -296,12 +295,10 @@ cudaError_t launch_staged_family(const HfracStagedLaunch &L, const CUtensorMap *
     constexpr int ZG = 4; // row groups per tile
     static_assert(SMEM <= 227 * 1024, "family boxes exceed shared memory");
     static_assert(G::W(K) <= 256, "box wider than a TMA box");
-    static std::once_flag once;
-    static cudaError_t attr = cudaSuccess;
-    std::call_once(once, [] {
-        attr = cudaFuncSetAttribute(hfrac_staged_kernel<H, TB, K, ZG>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-    });
+    // set on every launch (as for the stretch kernel): the attribute belongs
+    // to the current device's context
+    const cudaError_t attr = cudaFuncSetAttribute(
+        hfrac_staged_kernel<H, TB, K, ZG>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
     if (attr != cudaSuccess)
         return attr;
     HStagedParams<H, K> p;
@@ -344,25 +341,36 @@ struct MapCache {
     int nt = 0, H = 0, tb = 0;
     std::vector<CUtensorMap> maps;
 };
+constexpr int kMapCacheSlots = 4;
 
 template <int H, int TB>
 cudaError_t launch_staged_all(const HfracStagedLaunch &L, cudaStream_t s, int *launches)
 {
-    // the last plane's descriptors, per host thread (a plan runs on one
-    // thread at a time; equal address and layout give equal descriptors)
-    thread_local MapCache cache;
-    if (cache.fop != L.fop || cache.n != L.n || cache.ld != L.ld || cache.nt != L.nt ||
-        cache.H != H || cache.tb != TB) {
-        cache.fop = nullptr;
-        if (encode_all<H, TB>(L, cache.maps) != CUDA_SUCCESS)
+    // the descriptors of the last few planes, per host thread (equal address
+    // and layout give equal descriptors; a run encodes only a plane it has
+    // not seen, replacing the oldest entry)
+    thread_local MapCache caches[kMapCacheSlots];
+    thread_local int next_slot = 0;
+    MapCache *hit = nullptr;
+    for (MapCache &c : caches)
+        if (c.fop == L.fop && c.n == L.n && c.ld == L.ld && c.nt == L.nt && c.H == H &&
+            c.tb == TB)
+            hit = &c;
+    if (!hit) {
+        MapCache &c = caches[next_slot];
+        next_slot = (next_slot + 1) % kMapCacheSlots;
+        c.fop = nullptr;
+        if (encode_all<H, TB>(L, c.maps) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
-        cache.fop = L.fop;
-        cache.n = L.n;
-        cache.ld = L.ld;
-        cache.nt = L.nt;
-        cache.H = H;
-        cache.tb = TB;
+        c.fop = L.fop;
+        c.n = L.n;
+        c.ld = L.ld;
+        c.nt = L.nt;
+        c.H = H;
+        c.tb = TB;
+        hit = &c;
     }
+    MapCache &cache = *hit;
     cudaError_t e = cudaSuccess;
     int first = 0;
     static_for_host<0, n_heads(H)>([&](auto Ii) {
