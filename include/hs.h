@@ -411,7 +411,10 @@ HS_API hs_status hs_synth_fop(void *fop, float *fop32, int dtype, int n_template
  * [f_lo / m, f_hi / m) of level m, all below f_hi, so a band needs no data
  * from higher bands).  f_lo, and f_hi unless it equals n_bins, must be
  * multiples of hs_plan_tile_bins().  append != 0 keeps the buffer's count and
- * appends, so several bands can share one buffer.  Tiles run in linear order.
+ * appends, so several bands can share one buffer.  The band's tiles run in
+ * the plan's tile order restricted to the band (the staged kernel; a table
+ * the plan makes at the first run of each band -- make that run outside
+ * stream capture).
  * fop32: FP32 recheck copy for 16-bit plans, or NULL.
  * Errors: as hs_run_checked, and HS_ERR_INVALID for a bad range. */
 HS_API hs_status hs_run_range(hs_plan *p, const void *fop, const float *fop32, int64_t f_lo,

@@ -45,6 +45,9 @@ struct hs_plan {
         uint32_t *count = nullptr; // [0] pairs listed, [1] recheck blocks done
     };
     std::map<cudaStream_t, Pending> pend;
+    // tile order tables of partial ranges [tile_lo, tile_hi): the plan's order
+    // restricted to the range, made at the first run of that range
+    std::map<std::pair<int, int>, uint32_t *> range_orders;
     std::mutex mu;                 // guards the descriptor cache and streams
     const void *map_ptr = nullptr; // plane the cached descriptors encode
     CUtensorMap maps[kMaxStagedH];
@@ -197,9 +200,15 @@ namespace hs {
 // 0.14.
 std::vector<uint32_t> tile_order(int n_tiles, int kind)
 {
+    return tile_order_range(0, n_tiles, kind);
+}
+
+std::vector<uint32_t> tile_order_range(int tile_lo, int tile_hi, int kind)
+{
+    const int n_tiles = std::max(0, tile_hi - tile_lo);
     std::vector<uint32_t> o(n_tiles);
     for (int t = 0; t < n_tiles; ++t)
-        o[t] = (uint32_t)t;
+        o[t] = (uint32_t)(tile_lo + t);
     if (kind == 2) {
         auto key = [](uint32_t t) {
             if (t == 0)
@@ -220,9 +229,10 @@ std::vector<uint32_t> tile_order(int n_tiles, int kind)
         };
         std::vector<double> k(n_tiles);
         for (int t = 0; t < n_tiles; ++t)
-            k[t] = key((uint32_t)t);
-        std::stable_sort(o.begin(), o.end(),
-                         [&](uint32_t a, uint32_t b) { return k[a] < k[b]; });
+            k[t] = key((uint32_t)(tile_lo + t));
+        std::stable_sort(o.begin(), o.end(), [&](uint32_t a, uint32_t b) {
+            return k[a - (uint32_t)tile_lo] < k[b - (uint32_t)tile_lo];
+        });
     }
     return o;
 }
@@ -260,7 +270,8 @@ hs_status check_cands(const hs_cand_buf *c)
 }
 
 // Launch the plan's kernel over bins [f_lo, f_hi) (tile-aligned for the
-// staged kernel unless f_hi == n).  Linear order is used for partial ranges.
+// staged kernel unless f_hi == n).  A partial range runs the plan's order
+// restricted to its tiles (the harmonic-fraction map: linear).
 hs_status launch_range(hs_plan *p, const void *fop, const float *fop32, cudaStream_t s,
                        const hs_cand_buf *c, long long f_lo, long long f_hi, bool full)
 {
@@ -315,6 +326,30 @@ hs_status launch_range(hs_plan *p, const void *fop, const float *fop32, cudaStre
         L.ta = p->d_ta;
         L.fop32 = fop32;
         L.order = full ? p->d_order : nullptr;
+        L.tile_lo = (int)(f_lo / p->tb);
+        L.tile_hi = (int)((f_hi + p->tb - 1) / p->tb);
+        if (!full && p->d_order && p->opt.order != 1) {
+            // a band or chunk: the plan's order restricted to its tiles
+            const auto key = std::make_pair(L.tile_lo, L.tile_hi);
+            auto it = p->range_orders.find(key);
+            if (it == p->range_orders.end()) {
+                const int kind = p->opt.order != 0 ? p->opt.order : 3;
+                const std::vector<uint32_t> ord = tile_order_range(L.tile_lo, L.tile_hi, kind);
+                uint32_t *d = nullptr;
+                e = cudaMalloc(&d, sizeof(uint32_t) * std::max<size_t>(1, ord.size()));
+                if (e == cudaSuccess)
+                    e = cudaMemcpy(d, ord.data(), sizeof(uint32_t) * ord.size(),
+                                   cudaMemcpyHostToDevice);
+                if (e != cudaSuccess) {
+                    cudaFree(d);
+                    return cuda_fail(e, "tile order of a range");
+                }
+                it = p->range_orders.emplace(key, d).first;
+            }
+            L.order = it->second;
+            L.tile_hi -= L.tile_lo;
+            L.tile_lo = 0;
+        }
         L.delta = p->delta;
         L.band_abs = p->band_abs;
         L.rec = c->records;
@@ -322,8 +357,6 @@ hs_status launch_range(hs_plan *p, const void *fop, const float *fop32, cudaStre
         L.cap = c->capacity;
         L.n = p->n;
         L.ld = p->ld;
-        L.tile_lo = (int)(f_lo / p->tb);
-        L.tile_hi = (int)((f_hi + p->tb - 1) / p->tb);
         L.grid_per_sm = p->opt.grid_per_sm;
         L.ring_zs = p->ring_zs;
         L.assume_nonneg = p->opt.assume_nonneg != 0;
@@ -813,6 +846,8 @@ hs_status hs_plan_destroy(hs_plan *p)
         cudaFree(kv.second.pairs);
         cudaFree(kv.second.count);
     }
+    for (auto &kv : p->range_orders)
+        cudaFree(kv.second);
     for (cudaEvent_t ev : p->tev)
         cudaEventDestroy(ev);
     for (cudaEvent_t ev : p->chunk_events)

@@ -204,6 +204,9 @@ hs_status batch_set_prepared(hs_batch *b, const StagedBatchBeam *beams, int n_be
 // Shared host helpers (hs_api.cu)
 // Tile order of a plane of n_tiles tiles: 1 = linear, 2 = octave, 3 = semitone.
 std::vector<uint32_t> tile_order(int n_tiles, int kind);
+// The same order restricted to the tiles [tile_lo, tile_hi) (keys of their
+// own tile indices).
+std::vector<uint32_t> tile_order_range(int tile_lo, int tile_hi, int kind);
 CUresult encode_tensor_map(CUtensorMap *map, int dtype, const void *base, long long n_bins,
                            long long ld, int n_templates, int box_w, int box_rows);
 // The staged kernel's descriptors of one plane [sh.nt][n_bins] (row pitch
