@@ -65,6 +65,8 @@ namespace {
 // an FP32 copy): 2^19 pairs, 4 MiB.  A plane that marks more has the rest
 // decided inside the staged kernel.
 constexpr uint32_t kPendingPairs = 1u << 19;
+// Most tile-order tables of partial ranges a plan keeps at once.
+constexpr size_t kMaxRangeOrders = 64;
 
 thread_local std::string g_last_error;
 thread_local int g_last_launches = 0;
@@ -333,6 +335,17 @@ hs_status launch_range(hs_plan *p, const void *fop, const float *fop32, cudaStre
             const auto key = std::make_pair(L.tile_lo, L.tile_hi);
             auto it = p->range_orders.find(key);
             if (it == p->range_orders.end()) {
+                if (p->range_orders.size() >= kMaxRangeOrders) {
+                    // many distinct ranges (a sliding window, say): start over
+                    // rather than grow, once no stream of the device can still
+                    // read the old tables (rare: a device-wide wait)
+                    e = cudaDeviceSynchronize();
+                    if (e != cudaSuccess)
+                        return cuda_fail(e, "cudaDeviceSynchronize (range orders)");
+                    for (auto &kv : p->range_orders)
+                        cudaFree(kv.second);
+                    p->range_orders.clear();
+                }
                 const int kind = p->opt.order != 0 ? p->opt.order : 3;
                 const std::vector<uint32_t> ord = tile_order_range(L.tile_lo, L.tile_hi, kind);
                 uint32_t *d = nullptr;

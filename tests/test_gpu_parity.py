@@ -670,6 +670,26 @@ def test_plan_run_replays_in_a_cuda_graph(kind):
             assert st == hs.HS_OK and cnt == nref and np.array_equal(got, ref)
 
 
+def test_many_distinct_ranges_keep_their_records():
+    # more distinct bands than the plan keeps order tables for: the tables
+    # are dropped and made again, and every band's records stay those of the
+    # full run in that band
+    nt, n, H = 21, 128 * 80, 8
+    plane = synth.noise(nt, n, seed=15)
+    ta = synth.thresholds(1e-3, H, nt)
+    full, nfull, _, _ = run_gpu(plane, H, ta)
+    assert nfull > 0
+    fop = torch.from_numpy(plane).cuda()
+    cands = hs.CandBuffer(1 << 18)
+    with hs.Plan(nt, n, H, ta) as plan:
+        for lo in range(0, 70):  # 70 distinct bands of 10 tiles
+            a, b = 128 * lo, 128 * (lo + 10)
+            plan.run_range(fop, cands, a, b)
+            got, cnt, st = cands.fetch()
+            want = full[(full["bin"] >= a) & (full["bin"] < b)]
+            assert st == hs.HS_OK and np.array_equal(got, want)
+
+
 def test_launch_count_is_one():
     plane = synth.noise(21, 4096, seed=12)
     run_gpu(plane, 8, synth.thresholds(1e-3, 8, 21))
