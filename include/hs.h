@@ -164,7 +164,8 @@ HS_API hs_status hs_run(hs_plan *plan, const void *fop, hs_stream_t stream,
  * FP32 path's arithmetic, so the candidate set (and each record) equals
  * hs_run on the FP32 plane: the summing kernel lists the row pairs it marks
  * in a plan-owned list (one per stream, allocated at the first such run on
- * it, 4 MiB -- make that first run outside stream capture) and a second
+ * it, 4 MiB -- make that first run outside stream capture; past 16 streams
+ * the lists are freed after a device-wide wait and made again) and a second
  * kernel decides them from the copy (pairs past the list's 2^19 are decided
  * in the summing kernel).  When fop_f32 is NULL the 16-bit sums decide and
  * records carry HS_FLAG_LOWP (and HS_FLAG_NEAR inside the error band).  An

@@ -67,6 +67,8 @@ namespace {
 constexpr uint32_t kPendingPairs = 1u << 19;
 // Most tile-order tables of partial ranges a plan keeps at once.
 constexpr size_t kMaxRangeOrders = 64;
+// Most per-stream pending lists a plan keeps at once.
+constexpr size_t kMaxPendingLists = 16;
 
 thread_local std::string g_last_error;
 thread_local int g_last_launches = 0;
@@ -377,6 +379,18 @@ hs_status launch_range(hs_plan *p, const void *fop, const float *fop32, cudaStre
         L.nt_rt = p->nt;
         const bool defer = fop32 != nullptr && p->opt.dtype != HS_F32 && p->ring_stages == 0;
         if (defer) {
+            if (p->pend.size() >= kMaxPendingLists && p->pend.find(s) == p->pend.end()) {
+                // many streams (a new one per call, say): start over rather
+                // than keep 4 MiB for each, once no stream can still use them
+                e = cudaDeviceSynchronize();
+                if (e != cudaSuccess)
+                    return cuda_fail(e, "cudaDeviceSynchronize (pending lists)");
+                for (auto &kv : p->pend) {
+                    cudaFree(kv.second.pairs);
+                    cudaFree(kv.second.count);
+                }
+                p->pend.clear();
+            }
             hs_plan::Pending &pd = p->pend[s];
             if (!pd.pairs) {
                 // the count and the recheck kernel's done-counter start at

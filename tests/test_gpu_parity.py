@@ -272,6 +272,24 @@ def test_f16_overflow_is_decided_by_the_fp32_copy():
         {(int(x["z"]), int(x["bin"])) for x in at_inf if x["k"] == 1}
 
 
+def test_lowp_recheck_on_many_streams_of_one_plan():
+    # more streams than the plan keeps pending lists for: the lists are
+    # dropped and made again, and every run still gives the FP32 path's records
+    nt, n, H = 21, 8192, 8
+    plane = synth.noise(nt, n, seed=17)
+    ta = synth.thresholds(1e-3, H, nt)
+    ref, nref, _, _ = run_gpu(plane, H, ta)
+    low = torch.from_numpy(_bf16_bits(plane).view(np.int16)).cuda().view(torch.bfloat16)
+    f32 = torch.from_numpy(plane).cuda()
+    cands = hs.CandBuffer(1 << 16)
+    with hs.Plan(nt, n, H, ta, dtype="bf16") as plan:
+        for _ in range(20):
+            s = torch.cuda.Stream()
+            plan.run(low, cands, s, fop_f32=f32)
+            got, cnt, st = cands.fetch(s)
+            assert st == hs.HS_OK and cnt == nref and np.array_equal(got, ref)
+
+
 def test_lowp_recheck_on_two_streams_of_one_plan():
     # each stream has its own pending list: two 16-bit planes run on one plan
     # from two streams, repeatedly, each giving the FP32 path's records
