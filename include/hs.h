@@ -456,11 +456,15 @@ HS_API int hs_plan_kernel(const hs_plan *plan);
 /* Bins per CTA of the plan's kernel. */
 HS_API int hs_plan_tile_bins(const hs_plan *plan);
 
-/* Kernel timing for profiling.  While enabled, every kernel launch of the plan
- * is bracketed by CUDA events on its stream (kernels only: not the counter
- * reset or copies).  hs_plan_kernel_time waits for the recorded launches,
- * returns their summed device time in milliseconds and their number, and
- * clears the record.  Errors: HS_ERR_INVALID (null plan), HS_ERR_CUDA. */
+/* Kernel timing for profiling.  While enabled, the kernels of every run of the
+ * plan are bracketed by one pair of CUDA events on its stream (not the
+ * counter reset or copies; a run is one kernel, two for a 16-bit plane with
+ * an FP32 copy, one per level family for the harmonic-fraction map).  A pair
+ * costs a few microseconds of device time per run.  hs_plan_kernel_time
+ * waits for the recorded runs, returns their summed device time in
+ * milliseconds and their number, and clears the record (which grows by a
+ * pair of events per run until then).  Errors: HS_ERR_INVALID (null plan),
+ * HS_ERR_CUDA. */
 HS_API hs_status hs_plan_set_timing(hs_plan *plan, int enable);
 HS_API hs_status hs_plan_kernel_time(hs_plan *plan, double *total_ms, int *launches);
 
