@@ -184,6 +184,17 @@ def test_hfrac_padded_rows_never_read_the_pad():
     assert_matches_oracle(got, o, near)
 
 
+def test_hfrac_staged_at_the_largest_template_count():
+    # 32,767 templates (Z = 16,383): thousands of row blocks per family, the
+    # largest z a record holds; every level sum against the oracle
+    nt, n, H = 32767, 64, 8
+    plane = synth.noise(nt, n, seed=29)
+    got, used = _all_sums(plane, H, index="hfrac")
+    assert used == "staged"
+    ref = oracle.planes(plane, H, index=oracle.HFRAC)
+    np.testing.assert_allclose(got, ref, rtol=RTOL, atol=0)
+
+
 @pytest.mark.parametrize("nt,n,H", [(85, 1000, 16), (21, 777, 8), (127, 333, 16), (1, 50, 8)])
 def test_hfrac_gather_every_level_sum(nt, n, H):
     # the gather pair kernel: forced, or for rows that are not 16-byte multiples
