@@ -410,7 +410,8 @@ class Plan:
         hs_plan_set_timing(self.handle, enable)
 
     def kernel_time(self):
-        """(summed kernel ms, launches) recorded since the last call."""
+        """(summed device ms, runs) recorded since the last call while timing
+        was on (one event pair per run, around its kernels)."""
         return hs_plan_kernel_time(self.handle)
 
     def run_host(self, fop_host, fop_dev, cands: CandBuffer, host_records, stream=None,
