@@ -436,8 +436,7 @@ HS_API hs_status hs_run_range(hs_plan *p, const void *fop, const float *fop32, i
  *  - Every call looks up the array's device address with the caller's
  *    device current (cudaGetSymbolAddress), so a context made again after
  *    cudaDeviceReset gets the right one.  The first call on a device may load
- *    the library's module there: make that first call before any stream
- *    capture.
+ *    the library's module there.
  *  - All calls share the array and it keeps the last call's thresholds: two
  *    calls whose work overlaps on the GPU (different streams, or threads)
  *    race on it.  Serialise them, e.g. issue them on one stream.

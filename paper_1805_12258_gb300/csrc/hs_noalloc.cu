@@ -36,8 +36,7 @@ hs_status fail(hs_status s, const std::string &msg)
 // up on every call, with the caller's device current, so a context made
 // again (after cudaDeviceReset) never receives a stale address; after the
 // first call on a device the lookup is a host-side table read.  The first
-// call on a device may load the library's module there, which is why that
-// call should come before any stream capture.
+// call on a device may load the library's module there.
 hs_status table_address(float **out)
 {
     void *ptr = nullptr;
