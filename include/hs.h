@@ -87,7 +87,9 @@ typedef struct {
     int grid_per_sm;/* staged kernel: 0 = one CTA per tile; k > 0 = k resident CTAs per SM
                        that walk the tiles */
     int row_pitch;  /* elements between plane rows (0 = n_bins); >= n_bins.  The staged
-                       kernel needs row_pitch * element size to be a multiple of 16 bytes */
+                       kernel needs row_pitch * element size to be a multiple of 16 bytes
+                       (so its largest FP32 plane has 2^31 - 4 bins; wider planes take the
+                       generic kernel) */
     int stages;     /* staged kernel: 0 = one CTA per tile (or grid_per_sm); s > 0 = one
                        persistent CTA per SM with an s-stage ring of tiles, filled by a
                        producer warp while consumer groups sum (stretch map only) */

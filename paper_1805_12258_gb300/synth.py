@@ -91,6 +91,31 @@ def noise(n_templates: int, n_bins: int, seed: int, out: np.ndarray | None = Non
     return out
 
 
+def sparse_points(n_templates: int, n_bins: int, count: int, seed: int):
+    """`count` distinct (row, bin) positions of an n_templates x n_bins plane,
+    drawn uniformly without replacement, and an Exponential(mean 1) binary32
+    value for each: (rows int64, bins int64, values float32)."""
+    rng = np.random.Generator(np.random.Philox(key=[seed, 0x5A]))
+    flat = rng.choice(n_templates * n_bins, size=count, replace=False)
+    vals = rng.standard_exponential(count, dtype=np.float32)
+    return flat // n_bins, flat % n_bins, vals
+
+
+def sparse(n_templates: int, n_bins: int, count: int, seed: int,
+           ld: int | None = None) -> np.ndarray:
+    """A plane [n_templates][ld] (ld >= n_bins, the row pitch) that is zero
+    except at the positions and values of sparse_points; the padding bins
+    [n_bins, ld) stay zero.  The zeros are not written, so a very large
+    plane costs memory only where a value lies."""
+    ld = n_bins if ld is None else ld
+    if ld < n_bins:
+        raise ValueError("row pitch below the bin count")
+    out = np.zeros((n_templates, ld), np.float32)
+    rows, bins, vals = sparse_points(n_templates, n_bins, count, seed)
+    out[rows, bins] = vals
+    return out
+
+
 def draw_signals(wl: Workload, H_inj: int | None = None) -> list:
     """Random fundamentals with per-harmonic amplitudes U[3, 8]."""
     H_inj = wl.H if H_inj is None else H_inj

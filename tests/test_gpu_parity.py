@@ -841,3 +841,97 @@ def test_other_shapes_candidates(nt, n, H, assume_nonneg):
     assert used == "staged" and st == hs.HS_OK and cnt == len(recs) > 0
     ref, near = oracle.detect(plane, H, ta, threads=8)
     assert_matches_oracle(recs, ref, near)
+
+
+# --- the largest sizes a plan accepts ------------------------------------------
+
+def test_stretch_at_the_largest_template_count():
+    # 32,767 templates (z = -16,383 .. 16,383, the largest a record's 16-bit
+    # z holds): no staged family has that many rows, so the generic kernel
+    # runs; every level sum against the oracle
+    nt, n, H = 32767, 40, 16
+    plane = synth.noise(nt, n, seed=23)
+    got, used = _all_sums(plane, H)
+    assert used == "generic"
+    np.testing.assert_allclose(got, oracle.planes(plane, H), rtol=RTOL, atol=0)
+
+
+@pytest.fixture(scope="module")
+def max_bins():
+    # planes of one template row with a ragged last tile: 2^31 - 1 bins (the
+    # largest bin count; its rows are not 16-byte multiples, so the generic
+    # kernel runs) and 2^31 - 4 bins (the largest the FP32 staged kernel
+    # takes, whose rows must be 16-byte multiples with an int row pitch).
+    # Zero but for 3000 seeded exponential values below bin 2^31 - 4, so
+    # that only the touched pages hold memory.  The oracle's candidates at a
+    # threshold of 3 for every level over the whole smaller plane, and over
+    # the larger plane's three extra bins.
+    nt, H, count, seed = 1, 16, 3000, 31
+    n_big, n_staged = (1 << 31) - 1, (1 << 31) - 4
+    plane = synth.sparse(nt, n_staged, count, seed, ld=n_big)
+    ta = np.full((H, nt), 3.0, np.float32)
+    ref, near = oracle.detect(plane[:, :n_staged], H, ta, threads=16, cap=1 << 20)
+    tail, tail_near = oracle.detect(plane, H, ta, f_lo=n_staged)
+    assert len(ref) > 1000 and (ref["f"] >= (1 << 30)).any()
+    return dict(nt=nt, H=H, count=count, seed=seed, n_big=n_big, n_staged=n_staged, ta=ta,
+                ref=ref, near=near, tail=tail, tail_near=tail_near)
+
+
+def _sparse_on_device(m, n):
+    rows, bins, vals = synth.sparse_points(m["nt"], m["n_staged"], m["count"], m["seed"])
+    fop = torch.zeros((m["nt"], n), device="cuda")
+    fop[torch.from_numpy(rows).cuda(), torch.from_numpy(bins).cuda()] = \
+        torch.from_numpy(vals).cuda()
+    return fop
+
+
+def _run_max(m, n, **plan_kw):
+    fop = _sparse_on_device(m, n)
+    cands = hs.CandBuffer(1 << 20)
+    with hs.Plan(m["nt"], n, m["H"], m["ta"], **plan_kw) as plan:
+        plan.run(fop, cands)
+        recs, cnt, st = cands.fetch()
+        used = plan.kernel
+    del fop
+    torch.cuda.empty_cache()
+    assert st == hs.HS_OK and cnt == len(recs)
+    return recs, used
+
+
+@pytest.mark.parametrize("assume_nonneg", [True, False])
+def test_staged_at_the_largest_bin_count(max_bins, assume_nonneg):
+    m = max_bins
+    recs, used = _run_max(m, m["n_staged"], assume_nonneg=assume_nonneg)
+    assert used == "staged"
+    assert_matches_oracle(recs, m["ref"], m["near"])
+
+
+def test_generic_at_the_largest_bin_count(max_bins):
+    m = max_bins
+    recs, used = _run_max(m, m["n_big"])
+    assert used == "generic"
+    assert_matches_oracle(recs, np.concatenate([m["ref"], m["tail"]]),
+                          np.concatenate([m["near"], m["tail_near"]]))
+
+
+def test_hfrac_staged_at_the_largest_bin_count():
+    # the harmonic-fraction staged kernel forms f h in 32 bits, so it takes
+    # n_bins + tile <= 2^31 / H; the largest such plane (64-bin tiles, a
+    # ragged last tile, the row pitch padded to a 16-byte multiple)
+    nt, H, tb = 1, 16, 64
+    ld = (1 << 31) // H - tb
+    n = ld - 3
+    plane = synth.sparse(nt, n, 2000, seed=37, ld=ld)
+    ta = np.full((H, nt), 3.0, np.float32)
+    fop = torch.from_numpy(plane).cuda()
+    cands = hs.CandBuffer(1 << 20)
+    with hs.Plan(nt, n, H, ta, index="hfrac", row_pitch=ld) as plan:
+        assert plan.kernel == "staged" and plan.tile_bins == tb
+        plan.run(fop, cands)
+        recs, cnt, st = cands.fetch()
+    del fop
+    assert st == hs.HS_OK and cnt == len(recs)
+    ref, near = oracle.detect(plane[:, :n], H, ta, index=oracle.HFRAC, threads=16,
+                              cap=1 << 20)
+    assert len(ref) > 1000 and (ref["f"] >= (1 << 26)).any()
+    assert_matches_oracle(recs, ref, near)

@@ -82,3 +82,17 @@ def test_thresholds_are_per_level_and_row_independent():
 def test_random_plane_range():
     p = synth.random_plane(5, 1000, seed=2, lo=-1.0, hi=1.0)
     assert p.dtype == np.float32 and p.min() >= -1.0 and p.max() < 1.0 and p.min() < 0
+
+
+def test_sparse_plane_holds_its_points_and_zeros_elsewhere():
+    rows, bins, vals = synth.sparse_points(7, 1000, 300, seed=3)
+    assert len(set(zip(rows.tolist(), bins.tolist()))) == 300  # distinct positions
+    assert (rows >= 0).all() and (rows < 7).all() and (bins >= 0).all() and (bins < 1000).all()
+    assert vals.dtype == np.float32 and (vals >= 0).all()
+    p = synth.sparse(7, 1000, 300, seed=3, ld=1004)
+    assert p.shape == (7, 1004) and p.dtype == np.float32
+    assert np.array_equal(p[rows, bins], vals)
+    assert np.count_nonzero(p) == np.count_nonzero(vals) and not p[:, 1000:].any()
+    assert np.array_equal(p, synth.sparse(7, 1000, 300, seed=3, ld=1004))
+    with pytest.raises(ValueError):
+        synth.sparse(7, 1000, 3, seed=3, ld=999)
