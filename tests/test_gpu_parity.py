@@ -935,3 +935,35 @@ def test_hfrac_staged_at_the_largest_bin_count():
                               cap=1 << 20)
     assert len(ref) > 1000 and (ref["f"] >= (1 << 26)).any()
     assert_matches_oracle(recs, ref, near)
+
+
+@pytest.mark.parametrize("kind", ["staged", "generic", "hfrac", "bf16"])
+def test_count_only_buffer_counts_every_hit_and_writes_none(kind):
+    # a candidate buffer of capacity 0 with no records array: the run counts
+    # every hit and writes no record; hs_cand_sync reports the true count
+    # with HS_ERR_OVERFLOW.  The count equals a full buffer's and, but for
+    # near-threshold points, the oracle's.
+    nt, n, H = 21, 20000, 8
+    plane = synth.noise(nt, n, seed=41)
+    ta = synth.thresholds(1e-4, H, nt)
+    kw = {"staged": dict(kernel="staged"), "generic": dict(kernel="generic"),
+          "hfrac": dict(index="hfrac"), "bf16": dict(dtype="bf16")}[kind]
+    fop32 = torch.from_numpy(plane).cuda()
+    fop = fop32.to(torch.bfloat16) if kind == "bf16" else fop32
+    f32 = fop32 if kind == "bf16" else None
+    full = hs.CandBuffer(1 << 18)
+    counters = torch.zeros(4, dtype=torch.int32, device="cuda")
+    empty = hs.hs_cand_buf(None, counters.data_ptr(), 0)
+    with hs.Plan(nt, n, H, ta, **kw) as plan:
+        assert plan.kernel == ("generic" if kind == "generic" else "staged")
+        plan.run(fop, full, fop_f32=f32)
+        _, n_full, st_full = full.fetch()
+        if f32 is None:
+            hs.hs_run(plan.handle, fop, None, empty)
+        else:
+            hs.hs_run_checked(plan.handle, fop, f32, None, empty)
+        st, n_empty = hs.hs_cand_sync(empty, None)
+    assert st_full == hs.HS_OK and n_full > 100
+    assert st == hs.HS_ERR_OVERFLOW and n_empty == n_full
+    ref, near = oracle.detect(plane, H, ta, index=oracle.HFRAC if kind == "hfrac" else oracle.STRETCH)
+    assert abs(n_empty - len(ref)) <= len(near)
