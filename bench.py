@@ -225,18 +225,23 @@ def host_cores():
 KERNEL_SOURCES = ("hs_staged.cuh", "hs_device.cuh")
 
 
-def kernel_source_hash():
-    """Hash of the staged kernel's code (hs_staged.cuh + hs_device.cuh) with
-    comments and white space removed, so comment edits keep a profile valid."""
+def source_hash(files):
+    """Hash of the named csrc files' code with comments and white space
+    removed, so comment edits keep a profile valid."""
     import re
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in files:
         with open(os.path.join(ROOT, "paper_1805_12258_gb300", "csrc", f)) as fh:
             code = fh.read()
         code = re.sub(r"/\*.*?\*/", "", code, flags=re.S)
         code = re.sub(r"//[^\n]*", "", code)
         h.update(re.sub(r"\s+", "", code).encode())
     return h.hexdigest()[:16]
+
+
+def kernel_source_hash():
+    """Hash of the staged kernel's code (hs_staged.cuh + hs_device.cuh)."""
+    return source_hash(KERNEL_SOURCES)
 
 
 def profiled_traffic(name):
@@ -254,6 +259,44 @@ def profiled_traffic(name):
         if len(parts) >= 3 and parts[0] == name and parts[2] == sha:
             return int(parts[1])
     return None
+
+
+def profiled_instructions(name):
+    """Warp instructions per run (ncu smsp__inst_executed.sum over the run's
+    kernels) from profiles/instructions.txt, if taken on the current source of
+    the files the entry names; else None."""
+    path = os.path.join(ROOT, "profiles", "instructions.txt")
+    try:
+        with open(path) as fh:
+            lines = [ln.split("|") for ln in fh if ln.strip() and not ln.startswith("#")]
+    except OSError:
+        return None
+    for parts in lines:
+        parts = [x.strip() for x in parts]
+        if len(parts) >= 4 and parts[0] == name:
+            try:
+                if parts[2] == source_hash([f.strip() for f in parts[3].split(",")]):
+                    return int(parts[1])
+            except OSError:
+                return None
+    return None
+
+
+def issue_roofline(instructions, us, clk, sms):
+    """The instruction-issue roofline of a run: its warp instructions (ncu)
+    over its measured time, against one warp instruction per cycle on each of
+    the four schedulers of every SM at the SM clock sampled while it ran."""
+    mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz")
+    if not instructions or not mhz or not sms or us <= 0:
+        return None
+    achieved = instructions / (us / 1e6)
+    peak = sms * 4 * mhz * 1e6
+    return {"bound": "issue", "achieved": achieved, "peak": peak,
+            "unit": "warp-instructions/s", "frac": achieved / peak,
+            "instructions_per_run": instructions,
+            "peak_from": f"{sms} SMs x 4 schedulers x 1 warp-instruction per cycle x "
+                         f"{mhz:.0f} MHz (sampled)",
+            "instructions_from": "profiles/instructions.txt (ncu smsp__inst_executed.sum)"}
 
 
 def peaks():
@@ -326,6 +369,7 @@ def precision_summary(fop32, ta, H, ref_records, nonneg, steps=500):
     nt, n = fop32.shape
     stream = torch.cuda.current_stream()
     peak, kind = peaks()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     out = {}
     for dt, tdt in (("bf16", torch.bfloat16), ("f16", torch.float16)):
         low = fop32.to(tdt)
@@ -346,6 +390,8 @@ def precision_summary(fop32, ta, H, ref_records, nonneg, steps=500):
             torch.cuda.synchronize()
             clk = clocks.stop()
             recs, cnt, st = c.fetch(stream)
+            name = (f"staged {nt}x{n} H={H} {dt} tb={plan.tile_bins} "
+                    f"order={ORDER_NAMES[0]} with recheck")
         us = e0.elapsed_time(e1) / steps * 1e3
         algo = nt * n * 2 + H * nt * 4 + 16 * int(cnt) + 8
         out[dt] = {"storage": dt, "recheck": "FP32 copy", "mean_kernel_us": us,
@@ -357,6 +403,7 @@ def precision_summary(fop32, ta, H, ref_records, nonneg, steps=500):
                                 "frac": algo / (us / 1e6) / 1e9 / peak,
                                 "peak_kind": f"{kind} copy bandwidth",
                                 "algo_bytes_per_launch": algo},
+                   "issue_roofline": issue_roofline(profiled_instructions(name), us, clk, sms),
                    "clocks": clk}
         del low
     return out
@@ -395,13 +442,17 @@ def hfrac_summary(fop32, ta, H, stretch_us, steps=20):
         kernel, tb = plan.kernel, plan.tile_bins
     us = e0.elapsed_time(e1) / steps * 1e3
     algo = nt * n * 4 + H * nt * 4 + 16 * int(cnt) + 8
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    name = f"{kernel} hfrac {nt}x{n} H={H} f32 tb={tb}"
     return {"index": "hfrac", "kernel": kernel, "tile_bins": tb, "launches_per_run": launches,
             "mean_us_per_run": us, "points_per_s": nt * n / (us / 1e6),
             "level_sums_per_s": nt * n * H / (us / 1e6), "time_vs_stretch_map": us / stretch_us,
             "candidates": int(cnt), "status": hs.hs_status_str(st),
             "effective_hbm_gbs": algo / (us / 1e6) / 1e9,
             "frac_of_peak_on_unique_bytes": algo / (us / 1e6) / 1e9 / peak,
-            "peak_kind": f"{kind} copy bandwidth", "clocks": clk}, recs
+            "peak_kind": f"{kind} copy bandwidth",
+            "issue_roofline": issue_roofline(profiled_instructions(name), us, clk, sms),
+            "clocks": clk}, recs
 
 
 # ---- our arm ------------------------------------------------------------------------

@@ -63,6 +63,49 @@ def test_committed_traffic_table_is_well_formed():
         assert os.path.exists(os.path.join(bench.ROOT, "profiles", summary))
 
 
+def test_instructions_only_for_the_profiled_source(tmp_path, monkeypatch):
+    # an instruction count counts only for its run's name and the hash of
+    # the files its entry names; a code change in any of them voids it
+    files = ["hs_hfrac.cu", "hs_device.cuh"]
+    os.makedirs(os.path.join(tmp_path, CSRC))
+    for f in files:
+        shutil.copy(os.path.join(bench.ROOT, CSRC, f), os.path.join(tmp_path, CSRC, f))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    key = "staged hfrac 85x2097152 H=16 f32 tb=64"
+    os.makedirs(os.path.join(tmp_path, "profiles"))
+    with open(os.path.join(tmp_path, "profiles", "instructions.txt"), "w") as fh:
+        fh.write("# kernel | warp_instructions_per_run | source_sha | files | summary\n")
+        fh.write(f"{key} | 3600000000 | {bench.source_hash(files)} | {', '.join(files)} | x.md\n")
+        fh.write(f"{key.replace('64', '128')} | 1 | {bench.source_hash(files)} | missing.cu | y.md\n")
+    assert bench.profiled_instructions(key) == 3600000000
+    assert bench.profiled_instructions(key.replace("64", "128")) is None  # no such file
+    assert bench.profiled_instructions("staged 85x2097152 H=16 f32") is None
+    open(os.path.join(tmp_path, CSRC, "hs_hfrac.cu"), "a").write("\nstatic int changed;\n")
+    assert bench.profiled_instructions(key) is None
+
+
+def test_issue_roofline_arithmetic():
+    # 152 SMs x 4 schedulers x 2070 MHz = 1.25856e12 warp-instructions/s
+    r = bench.issue_roofline(1.25856e9, 1000.0, {"sm_mhz": 2070.0}, 152)
+    assert r["bound"] == "issue" and r["peak"] == 152 * 4 * 2070e6
+    assert abs(r["achieved"] - 1.25856e12) < 1.0 and abs(r["frac"] - 1.0) < 1e-12
+    assert bench.issue_roofline(None, 1000.0, {"sm_mhz": 2070.0}, 152) is None
+    assert bench.issue_roofline(1e9, 1000.0, {}, 152) is None
+
+
+def test_committed_instruction_table_is_well_formed():
+    with open(os.path.join(bench.ROOT, "profiles", "instructions.txt")) as fh:
+        rows = [ln.split("|") for ln in fh if ln.strip() and not ln.startswith("#")]
+    assert rows
+    for r in rows:
+        name, inst, sha, files, summary = (x.strip() for x in r)
+        assert name.startswith("staged ") and int(inst) > 0
+        assert len(sha) == 16 and int(sha, 16) >= 0
+        for f in files.split(","):
+            assert os.path.exists(os.path.join(bench.ROOT, CSRC, f.strip()))
+        assert os.path.exists(os.path.join(bench.ROOT, "profiles", summary))
+
+
 def test_order_names():
     assert bench.ORDER_NAMES[0] == bench.ORDER_NAMES[3] == "semitone"
     assert bench.ORDER_NAMES[1] == "linear" and bench.ORDER_NAMES[2] == "octave"
