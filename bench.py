@@ -52,7 +52,7 @@ sys.path.insert(0, ROOT)
 METRIC = "FOP points harmonic-summed/s (H=16) and effective HBM GB/s vs 8 TB/s"
 UNIT = "points/s"
 L2_BYTES = 129 * 2**20
-ORDER_NAMES = {0: "semitone", 1: "linear", 2: "octave", 3: "semitone"}
+ORDER_NAMES = {0: "53-step", 1: "linear", 2: "octave", 3: "semitone", 4: "53-step"}
 
 
 def parse():

@@ -81,9 +81,10 @@ typedef struct {
                        H = 8 or 16 with symmetric rounding, its gather form. */
     int tile_bins;  /* bins per CTA of the staged kernel: 0 = default (128; 64 for
                        HS_INDEX_HFRAC, which takes 64 or 128) */
-    int order;      /* tile order: 0 = default (semitone; linear for HS_INDEX_HFRAC),
+    int order;      /* tile order: 0 = default (4; linear for HS_INDEX_HFRAC),
                        1 = linear, 2 = octave (mantissa of the tile index), 3 = semitone
-                       (fractional part of 12 log2 of the tile index) */
+                       (fractional part of 12 log2 of the tile index), 4 = the same with
+                       53 steps to the octave (fractional part of 53 log2) */
     int grid_per_sm;/* staged kernel: 0 = one CTA per tile; k > 0 = k resident CTAs per SM
                        that walk the tiles */
     int row_pitch;  /* elements between plane rows (0 = n_bins); >= n_bins.  The staged

@@ -26,8 +26,8 @@ _lock = threading.Lock()
 # launch forms: one CTA per tile, resident CTAs walking tiles, pipelined ring
 LAUNCH_FORMS = ({"grid_per_sm": 0}, {"grid_per_sm": 3}, {"stages": 3, "z_split": 2},
                 {"stages": 3, "z_split": 3})
-PLANE_SPACE = {"tile_bins": (64, 96, 128), "order": (1, 2, 3), "launch": LAUNCH_FORMS}
-BATCH_SPACE = {"form": ("packed", "beams"), "order": (2, 3), "grid_per_sm": (0, 3)}
+PLANE_SPACE = {"tile_bins": (64, 96, 128), "order": (1, 2, 3, 4), "launch": LAUNCH_FORMS}
+BATCH_SPACE = {"form": ("packed", "beams"), "order": (2, 3, 4), "grid_per_sm": (0, 3)}
 
 
 def cache_path() -> str:

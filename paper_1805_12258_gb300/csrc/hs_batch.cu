@@ -143,7 +143,7 @@ hs_status hs_batch_create(hs_batch **out, int n_templates, int H, const float *t
         if (!std::isfinite(thresholds[i]))
             return fail(HS_ERR_INVALID, "thresholds must be finite");
     if (o.dtype < HS_F32 || o.dtype > HS_F16 || o.grid_per_sm < 0 || o.grid_per_sm > 64 ||
-        o.order < 0 || o.order > 3 || o.assume_nonneg < 0 || o.assume_nonneg > 1)
+        o.order < 0 || o.order > 4 || o.assume_nonneg < 0 || o.assume_nonneg > 1)
         return fail(HS_ERR_INVALID, "unknown option value");
     const StagedShape sh{n_templates, H, 128, o.dtype};
     if (!staged_batch_available(sh) || o.index != HS_INDEX_STRETCH ||
@@ -156,7 +156,7 @@ hs_status hs_batch_create(hs_batch **out, int n_templates, int H, const float *t
     b->nt = n_templates;
     b->H = H;
     b->dtype = o.dtype;
-    b->order = o.order == 0 ? 3 : o.order; // default: semitone
+    b->order = o.order == 0 ? 4 : o.order; // default: 53 steps to the octave
     b->assume_nonneg = o.assume_nonneg != 0;
     b->max_beams = max_beams;
     b->ta.assign(thresholds, thresholds + (size_t)H * n_templates);

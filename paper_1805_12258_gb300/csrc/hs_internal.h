@@ -202,7 +202,8 @@ hs_status batch_set_prepared(hs_batch *b, const StagedBatchBeam *beams, int n_be
                              cudaStream_t s);
 
 // Shared host helpers (hs_api.cu)
-// Tile order of a plane of n_tiles tiles: 1 = linear, 2 = octave, 3 = semitone.
+// Tile order of a plane of n_tiles tiles: 1 = linear, 2 = octave, 3 = semitone,
+// 4 = 53 steps to the octave.
 std::vector<uint32_t> tile_order(int n_tiles, int kind);
 // The same order restricted to the tiles [tile_lo, tile_hi) (keys of their
 // own tile indices).

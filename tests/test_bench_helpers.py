@@ -107,7 +107,8 @@ def test_committed_instruction_table_is_well_formed():
 
 
 def test_order_names():
-    assert bench.ORDER_NAMES[0] == bench.ORDER_NAMES[3] == "semitone"
+    assert bench.ORDER_NAMES[0] == bench.ORDER_NAMES[4] == "53-step"
+    assert bench.ORDER_NAMES[3] == "semitone"
     assert bench.ORDER_NAMES[1] == "linear" and bench.ORDER_NAMES[2] == "octave"
 
 

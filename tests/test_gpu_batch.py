@@ -66,7 +66,8 @@ def test_batch_matches_per_plane_runs_and_graph_replay(nt, H, gps, nonneg):
                 assert np.array_equal(got, _plan_records(plane, H, ta))
 
 
-@pytest.mark.parametrize("nt,H,order", [(85, 16, 0), (21, 8, 0), (85, 16, 1), (85, 16, 3)])
+@pytest.mark.parametrize("nt,H,order", [(85, 16, 0), (21, 8, 0), (85, 16, 1), (85, 16, 3),
+                                        (85, 16, 2)])
 def test_batch_spanning_several_launches(nt, H, order):
     # more beams than one launch's parameter block holds: the run splits them
     # over launches; graph replays, and re-captures after the beam set

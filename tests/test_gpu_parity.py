@@ -593,11 +593,11 @@ def test_pipelined_matches_oracle_on_the_small_ska_slice():
     assert_matches_oracle(recs, ref, near)
 
 
-@pytest.mark.parametrize("order", [2, 3])
+@pytest.mark.parametrize("order", [2, 3, 4])
 @pytest.mark.parametrize("n", [1 << 15, (1 << 15) + 128, 1 << 18])
 def test_tile_orders_give_the_same_records(n, order):
-    # the octave and semitone orders (the plan's tile table) visit every tile
-    # exactly once: the same records as the linear order
+    # the octave, semitone and 53-step orders (the plan's tile table) visit
+    # every tile exactly once: the same records as the linear order
     plane = synth.noise(85, n, seed=29)
     ta = synth.thresholds(1e-4, 16, 85)
     lin, nl, _, _ = run_gpu(plane, 16, ta, order=1)
@@ -743,7 +743,8 @@ def ska_oracle(ska):
 
 
 # assume_nonneg=True is the launch configuration bench.py times (no sign
-# check, level 1 in row bands, semitone tile order); False the checked one.
+# check, level 1 in row bands, the default 53-step tile order); False the
+# checked one.
 @pytest.mark.parametrize("assume_nonneg", [True, False])
 def test_ska_plane_candidates(ska, ska_oracle, assume_nonneg):
     wl, plane, ta = ska

@@ -223,23 +223,27 @@ def octave_key(t):
     return (t / 2.0 ** e, e)
 
 
-def semitone_key(t):
+def semitone_key(t, steps=12.0):
     if t == 0:
         return -1.0
-    x = 12.0 * math.log2(t)
+    x = steps * math.log2(t)
     return x - math.floor(x)
+
+
+def step53_key(t):
+    return semitone_key(t, 53.0)
 
 
 @pytest.mark.parametrize("n", [0, 1, 2, 7, 1000, 16384])
 def test_tile_orders(n):
     lin = hs.hs_tile_order(n, 1)
     assert np.array_equal(lin, np.arange(n, dtype=np.uint32))
-    for order, key in ((2, octave_key), (3, semitone_key)):
+    for order, key in ((2, octave_key), (3, semitone_key), (4, step53_key)):
         o = hs.hs_tile_order(n, order)
         assert np.array_equal(np.sort(o), np.arange(n, dtype=np.uint32))
         keys = [key(int(t)) for t in o]
         assert all(a <= b for a, b in zip(keys, keys[1:]))
-    assert np.array_equal(hs.hs_tile_order(n, 0), hs.hs_tile_order(n, 3))
+    assert np.array_equal(hs.hs_tile_order(n, 0), hs.hs_tile_order(n, 4))
 
 
 def test_semitone_order_keeps_thirds_close():
@@ -257,8 +261,23 @@ def test_semitone_order_keeps_thirds_close():
     assert np.median(pos[3]) < 0.05 < np.median(pos[2])
 
 
+def test_53_step_order_keeps_fifths_closer():
+    # tiles t and 5t (the span of m = 5 of tile 5t is tile t's level 1):
+    # 2^(123/53) = 4.99 against 2^(28/12) = 5.04, so the 53-step order visits
+    # them nearer together than the semitone order does
+    n = 16384
+    pos = {}
+    for order in (3, 4):
+        o = hs.hs_tile_order(n, order)
+        p = np.empty(n, np.int64)
+        p[o] = np.arange(n)
+        t = np.arange(n // 16, n // 5)
+        pos[order] = np.abs(p[5 * t] - p[t]) / n
+    assert np.median(pos[4]) < np.median(pos[3])
+
+
 def test_tile_order_validation():
     with pytest.raises(hs.HsError):
-        hs.hs_tile_order(10, 4)
+        hs.hs_tile_order(10, 5)
     with pytest.raises(hs.HsError):
         hs.hs_tile_order(-1, 1)
