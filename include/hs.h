@@ -137,7 +137,9 @@ typedef struct hs_plan hs_plan;
  *  thresholds  : host array TA[H][n_templates] (level-major, binary32, all
  *                finite); copied, the caller keeps ownership.
  *  opt         : NULL for defaults.
- * Allocates the plan's device tables on the current device.
+ * Allocates the plan's device tables on the current device; the plan runs
+ * only with that device current (any other gives HS_ERR_INVALID, and
+ * hs_plan_destroy frees on the plan's device whatever device is current).
  * Errors: HS_ERR_INVALID, HS_ERR_UNSUPPORTED (kernel = STAGED, or stages > 0,
  *         where no such kernel applies), HS_ERR_OOM, HS_ERR_CUDA. */
 HS_API hs_status hs_plan_create(hs_plan **out, int n_templates, int64_t n_bins, int H,
@@ -241,7 +243,10 @@ typedef struct hs_batch hs_batch;
  * (tile order inside each beam, as for a plan), grid_per_sm (0 = one CTA
  * per tile; k > 0 = k resident CTAs per SM) and assume_nonneg (as for a
  * plan).  Compiled shapes: 85 x 16 (FP32,
- * BF16) and 21 x 8 (FP32), stretch index map, symmetric rounding.
+ * BF16) and 21 x 8 (FP32), stretch index map, symmetric rounding.  Like a
+ * plan, a batch belongs to the device current at its creation: the other
+ * hs_batch_* calls need that device current (else HS_ERR_INVALID), and
+ * hs_batch_destroy frees on it.
  * Errors: HS_ERR_INVALID, HS_ERR_UNSUPPORTED, HS_ERR_OOM, HS_ERR_CUDA. */
 HS_API hs_status hs_batch_create(hs_batch **out, int n_templates, int H, const float *thresholds,
                                  const hs_options *opt, int max_beams);

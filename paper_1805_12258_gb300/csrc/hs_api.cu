@@ -267,6 +267,20 @@ hs_status encode_maps(hs_plan *p, const void *fop)
     return HS_OK;
 }
 
+// A plan's tables live on the device that was current when it was made; a
+// kernel launched with another device current would read them from there.
+hs_status check_device(const hs_plan *p)
+{
+    int dev = -1;
+    const cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaGetDevice");
+    if (dev != p->device)
+        return fail(HS_ERR_INVALID, "the plan belongs to another device: make that device "
+                                    "current before running it");
+    return HS_OK;
+}
+
 hs_status check_cands(const hs_cand_buf *c)
 {
     if (!c || !c->count)
@@ -656,6 +670,8 @@ hs_status hs_run_checked(hs_plan *p, const void *fop, const float *fop32, hs_str
     g_last_launches = 0;
     if (!p)
         return fail(HS_ERR_INVALID, "plan is null");
+    if (hs_status d = check_device(p); d != HS_OK)
+        return d;
     if (!fop || reinterpret_cast<uintptr_t>(fop) % 16 != 0)
         return fail(HS_ERR_INVALID, "plane pointer must be non-null and 16-byte aligned");
     if (fop32 && p->opt.dtype == HS_F32)
@@ -684,6 +700,8 @@ hs_status hs_run_range(hs_plan *p, const void *fop, const float *fop32, int64_t 
     g_last_launches = 0;
     if (!p)
         return fail(HS_ERR_INVALID, "plan is null");
+    if (hs_status d = check_device(p); d != HS_OK)
+        return d;
     if (!fop || reinterpret_cast<uintptr_t>(fop) % 16 != 0)
         return fail(HS_ERR_INVALID, "plane pointer must be non-null and 16-byte aligned");
     if (fop32 && (p->opt.dtype == HS_F32 || reinterpret_cast<uintptr_t>(fop32) % 16 != 0))
@@ -743,6 +761,8 @@ hs_status hs_run_host_checked(hs_plan *p, const void *fop_host, void *fop_dev,
     g_last_launches = 0;
     if (!p || !fop_host || !fop_dev)
         return fail(HS_ERR_INVALID, "plan, host plane and device plane must be non-null");
+    if (hs_status d = check_device(p); d != HS_OK)
+        return d;
     const float *fop32_dev = nullptr;
     if (fop32_host) {
         if (p->opt.dtype == HS_F32)
@@ -871,6 +891,10 @@ hs_status hs_plan_destroy(hs_plan *p)
 {
     if (!p)
         return HS_OK;
+    // synchronise and free on the plan's own device
+    int cur = -1;
+    const bool other = cudaGetDevice(&cur) == cudaSuccess && cur != p->device &&
+                       cudaSetDevice(p->device) == cudaSuccess;
     cudaDeviceSynchronize();
     cudaFree(p->d_ta);
     cudaFree(p->d_order);
@@ -887,6 +911,8 @@ hs_status hs_plan_destroy(hs_plan *p)
     if (p->copy_stream)
         cudaStreamDestroy(p->copy_stream);
     delete p;
+    if (other)
+        cudaSetDevice(cur);
     return HS_OK;
 }
 

@@ -35,6 +35,7 @@ struct hs_batch {
     int grid_per_sm = 0;         // 0: one CTA per tile
     bool assume_nonneg = false;  // planes declared non-negative: no sign check
     int sms = 0;
+    int device = 0;              // the device current at creation: its tables live there
     std::mutex mu;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -71,6 +72,20 @@ hs_status cuda_fail(cudaError_t e, const char *what)
 }
 
 size_t elem_size(int dtype) { return dtype == HS_F32 ? 4 : 2; }
+
+// A batch's tables live on the device that was current when it was made; a
+// kernel launched with another device current would read them from there.
+hs_status check_device(const hs_batch *b)
+{
+    int dev = -1;
+    const cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaGetDevice");
+    if (dev != b->device)
+        return fail(HS_ERR_INVALID, "the batch belongs to another device: make that device "
+                                    "current before using it");
+    return HS_OK;
+}
 
 StagedBatch launch_args(const hs_batch *b)
 {
@@ -164,6 +179,7 @@ hs_status hs_batch_create(hs_batch **out, int n_templates, int H, const float *t
     group_bounds(b->ta.data(), n_templates, H, b->delta, b->band_abs, b->tmin);
     int dev = 0;
     cudaGetDevice(&dev);
+    b->device = dev;
     cudaError_t e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
     b->grid_per_sm = o.grid_per_sm;
     if (e == cudaSuccess)
@@ -249,6 +265,8 @@ hs_status hs_batch_set_beams(hs_batch *b, const hs_beam *beams, int n_beams, hs_
 {
     if (!b || (!beams && n_beams > 0))
         return fail(HS_ERR_INVALID, "batch or beams is null");
+    if (hs_status d = check_device(b); d != HS_OK)
+        return d;
     if (n_beams < 0 || n_beams > b->max_beams)
         return fail(HS_ERR_INVALID, "n_beams must be in [0, max_beams]");
     const size_t es = elem_size(b->dtype);
@@ -291,6 +309,8 @@ hs_status hs_batch_set_packed(hs_batch *b, const void *plane, const float *fop32
 {
     if (!b || (!beams && n_beams > 0))
         return fail(HS_ERR_INVALID, "batch or beams is null");
+    if (hs_status d = check_device(b); d != HS_OK)
+        return d;
     if (n_beams < 0 || n_beams > b->max_beams)
         return fail(HS_ERR_INVALID, "n_beams must be in [0, max_beams]");
     const long long es = (long long)elem_size(b->dtype);
@@ -406,6 +426,8 @@ hs_status hs_batch_run(hs_batch *b, hs_stream_t stream)
 {
     if (!b)
         return fail(HS_ERR_INVALID, "batch is null");
+    if (hs_status d = check_device(b); d != HS_OK)
+        return d;
     std::lock_guard<std::mutex> lk(b->mu);
     cudaError_t e = launch_run(b, reinterpret_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? HS_OK : cuda_fail(e, "batched kernel launch");
@@ -415,6 +437,8 @@ hs_status hs_batch_graph_run(hs_batch *b, hs_stream_t stream)
 {
     if (!b)
         return fail(HS_ERR_INVALID, "batch is null");
+    if (hs_status d = check_device(b); d != HS_OK)
+        return d;
     std::lock_guard<std::mutex> lk(b->mu);
     cudaError_t e = cudaSuccess;
     if (b->graph_stale || !b->gexec) {
@@ -467,6 +491,10 @@ hs_status hs_batch_destroy(hs_batch *b)
 {
     if (!b)
         return HS_OK;
+    // synchronise and free on the batch's own device
+    int cur = -1;
+    const bool other = cudaGetDevice(&cur) == cudaSuccess && cur != b->device &&
+                       cudaSetDevice(b->device) == cudaSuccess;
     cudaDeviceSynchronize();
     if (b->gexec)
         cudaGraphExecDestroy(b->gexec);
@@ -477,6 +505,8 @@ hs_status hs_batch_destroy(hs_batch *b)
     cudaFree(b->d_pbeams);
     cudaFree(b->d_ptiles);
     delete b;
+    if (other)
+        cudaSetDevice(cur);
     return HS_OK;
 }
 
