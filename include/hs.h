@@ -119,7 +119,8 @@ typedef struct {
 } hs_cand;
 
 /* Caller-owned device candidate buffer.
- *  records : device array of `capacity` records.
+ *  records : device array of `capacity` records (NULL with capacity 0: a
+ *            count-only buffer; runs then count every hit and write none).
  *  count   : device array of 2 uint32: [0] = number of candidates found
  *            (may exceed capacity; records beyond it are dropped),
  *            [1] = device status (HS_OK or HS_ERR_TIMEOUT).
